@@ -1,0 +1,430 @@
+"""Benchmark of the fused fluctuating central-moment LBM step on GB300.
+
+Workload (one "step" = one lattice update of every site, the whole hot path, with the
+statistics reduction on every `stats_every`-th step): D3Q27 256^3 periodic box, FP32
+deviations in one AA-pattern array (1.81 GB, far above the 129 MB L2, so no flush is
+needed between steps), rho0 = 1 with a seeded 1e-3 uniform density perturbation, drift
+u0 = (0.05, 0.02, 0), kBT = 1e-4, shear rate omega = 1.6 (Lambda_7-9), all other modes 1.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). N > 1 runs N independent replicas (one lattice per
+GPU, weak scaling, no data exchange) launched by torch.distributed.run.
+`--impl reference` times the FP64 CPU oracle on this host's cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fluctuating D3Q27 GLUPS and fraction of HBM roofline at stated oracle error"
+UNIT = "GLUPS"
+DIMS = (256, 256, 256)  # overridable with --dims for profiling runs on smaller boxes
+KBT = 1e-4
+OMEGA = 1.6
+U0 = (0.05, 0.02, 0.0)
+AMP = 1e-3
+SEED = 0
+BYTES_PER_SITE = 27 * 4 * 2  # read + write of 27 FP32 populations (noise is generated, not stored)
+
+
+def lam_d3q27(omega=OMEGA):
+    lam = np.ones(27)
+    lam[[7, 8, 9]] = omega
+    return lam
+
+
+def workload_config(stats_every, world, dims=DIMS):
+    return {
+        "workload": "D3Q27 256^3 periodic fluctuating central-moment LBM, FP32 AA-pattern, "
+                    "rho0=1 +1e-3 seeded perturbation, drift (0.05,0.02,0), kBT=1e-4, shear omega=1.6",
+        "lattice": "D3Q27",
+        "dims": list(dims),
+        "storage": "fp32 deviations f_i - w_i rho0, one in-place AA array",
+        "kBT": KBT,
+        "omega_shear": OMEGA,
+        "u0": list(U0),
+        "rho_perturb": AMP,
+        "stats_every": stats_every,
+        "l2": "inputs larger than L2 (1.81 GB state vs 129 MB L2); no flush",
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+    }
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2602_16486_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per step-kernel launch from an ncu capture, if it was taken on the
+    current kernel sources (profiles/step_traffic.json), else None."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh)
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("bytes_per_launch_256cube")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.seek(0)
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxes.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxes), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2602_16486_gb300 as fl
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    dims = tuple(args.dims)
+    sites = dims[0] * dims[1] * dims[2]
+    S = args.stats_every
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    lat = fl.Lattice(fl.FLBM_D3Q27, dims, lam_d3q27(), KBT, 1.0, SEED + rank, fl.FLBM_FP32,
+                     cuda_stream=stream.cuda_stream)
+    fl.flbm_set_sample_capacity(lat.ctx, max(1, (args.steps + args.warmup) // S + 2))
+    lat.init_uniform(U0, AMP, SEED + rank)
+
+    def one_step(k):
+        lat.step(1)
+        if k % S == 0:
+            lat.sample()
+
+    for k in range(args.warmup):
+        one_step(k)
+    lat.fetch_samples()
+    stream.synchronize()
+
+    # ---- device-timed region: K steps, inputs resident in HBM ---------------------------
+    ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(dev)).split(",")[dev if world == 1 else local]
+    barrier()
+    torch.cuda.synchronize()
+    launches = 0
+    with ClockSampler(gpu_index) as clocks:
+        t0.record(stream)
+        for k in range(args.steps):
+            ev_k[k][0].record(stream)
+            lat.step(1)
+            ev_k[k][1].record(stream)
+            launches += 1
+            if k % S == 0:
+                lat.sample()
+                launches += 1
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    elapsed_ms = t0.elapsed_time(t1)
+    step_kernel_ms = [a.elapsed_time(b) for a, b in ev_k]
+    samples = lat.fetch_samples()
+    nonfinite = sum(s["nonfinite"] for s in samples)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    # ---- end to end through the C ABI with host buffers ---------------------------------
+    if args.no_e2e:
+        lat.close()
+        if rank != 0:
+            return None
+        return {"metric": METRIC, "value": sites * args.steps / (elapsed_ms * 1e-3) / 1e9, "unit": UNIT,
+                "dims": list(dims), "avg_step_kernel_ms": float(np.mean(step_kernel_ms)),
+                "note": "profiling run (--no-e2e): not a bench line"}
+    nbytes = fl.flbm_checkpoint_bytes(lat.ctx)
+    host_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    host_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    fl.flbm_save(lat.ctx, host_in.data_ptr(), nbytes)
+    n_e2e = args.steps
+    stats_bytes = 0
+    barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    fl.flbm_load(lat.ctx, host_ptr=host_in.data_ptr(), nbytes=nbytes)
+    for k in range(n_e2e):
+        lat.step(1)
+        if k % S == 0:
+            lat.stats()
+            stats_bytes += (14 + 27 + 27 * 28 // 2 + 1) * 8
+    fl.flbm_save(lat.ctx, host_out.data_ptr(), nbytes)
+    e2e_s = time.perf_counter() - w0
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    lat.close()
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return None
+
+    value = world * sites * args.steps / (elapsed_ms * 1e-3) / 1e9
+    avg_kernel_ms = float(np.mean(step_kernel_ms))
+    peaks, peak_kind = measured_peaks()
+    achieved = BYTES_PER_SITE * sites / (avg_kernel_ms * 1e-3) / 1e9
+    roof = {
+        "bound": "hbm",
+        "achieved": round(achieved, 1),
+        "peak": peaks["hbm_gbs"],
+        "unit": "GB/s",
+        "frac": round(achieved / peaks["hbm_gbs"], 4),
+        "traffic": recorded_traffic(),
+        "kernel": "step_kernel<D3Q27, fp32> (fused collide + AA stream)",
+        "peak_kind": f"{peak_kind} STREAM-style copy (hbm_gbs)",
+        "algorithmic_bytes_per_launch": BYTES_PER_SITE * sites,
+        "avg_launch_ms": round(avg_kernel_ms, 5),
+    }
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded lattice state, no dataset)",
+        "config": workload_config(S, world, dims),
+        "roofline": roof,
+        "e2e": {
+            "value": round(world * sites * n_e2e / e2e_s / 1e9, 3),
+            "unit": UNIT,
+            "h2d_bytes_per_step": int(nbytes / n_e2e),
+            "d2h_bytes_per_step": int((nbytes + stats_bytes) / n_e2e),
+            "what": "flbm_load from pinned host blob, K x flbm_step(1) with flbm_stats every "
+                    f"{S} steps (sync + D2H), flbm_save to pinned host; wall clock",
+        },
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+        "nonfinite_sites_in_samples": int(nonfinite),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return line
+
+
+# ---- the oracle on the host cores ---------------------------------------------------------
+def _oracle_sample_dims(target_sites):
+    # A cube-ish D3Q27 box of about target_sites sites (same physics as the workload).
+    n = max(4, int(round(target_sites ** (1.0 / 3.0))))
+    return (n, n, n)
+
+
+def cpu_baseline(budget_s=15.0):
+    """Time the oracle (as it stands) on a bounded sample of the workload."""
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    lam = lam_d3q27()
+    # Calibrate on a small box, then size the sample for about budget_s seconds.
+    cal = (16, 16, 16)
+    f = oracle.init_uniform(1, cal, 1.0, U0, AMP, SEED)
+    t = time.perf_counter()
+    oracle.run(1, cal, lam, KBT, SEED, f, 0, 1, threads=threads)
+    per_site = (time.perf_counter() - t) / np.prod(cal)
+    steps = 4
+    dims = _oracle_sample_dims(min(budget_s / (per_site * steps), 64 ** 3))
+    f = oracle.init_uniform(1, dims, 1.0, U0, AMP, SEED)
+    t = time.perf_counter()
+    oracle.run(1, dims, lam, KBT, SEED, f, 0, steps, threads=threads)
+    dt = time.perf_counter() - t
+    value = np.prod(dims) * steps / dt / 1e9
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"D3Q27 {dims[0]}x{dims[1]}x{dims[2]} (same physics as the workload), "
+                      f"{steps} steps, {dt:.1f} s, FP64 dense T(u)+LU, OpenMP over sites"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return None
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    lam = lam_d3q27()
+    cal = (16, 16, 16)
+    f = oracle.init_uniform(1, cal, 1.0, U0, AMP, SEED)
+    t = time.perf_counter()
+    oracle.run(1, cal, lam, KBT, SEED, f, 0, 1, threads=threads)
+    per_site = (time.perf_counter() - t) / np.prod(cal)
+    total_budget = args.ref_budget
+    dims = _oracle_sample_dims(max(512, min(total_budget / max(1, args.steps + args.warmup) / per_site,
+                                            64 ** 3)))
+    f = oracle.init_uniform(1, dims, 1.0, U0, AMP, SEED)
+    for k in range(args.warmup):
+        f = oracle.run(1, dims, lam, KBT, SEED, f, k, 1, threads=threads)
+    t = time.perf_counter()
+    for k in range(args.steps):
+        f = oracle.run(1, dims, lam, KBT, SEED, f, args.warmup + k, 1, threads=threads)
+    dt = time.perf_counter() - t
+    sites = int(np.prod(dims))
+    value = sites * args.steps / dt / 1e9
+    sample = (f"D3Q27 {dims[0]}x{dims[1]}x{dims[2]} per step (bounded sample of the 256^3 workload, "
+              "same physics), FP64 oracle, OpenMP over sites")
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded lattice state, no dataset)",
+        "config": workload_config(1, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--stats-every", type=int, default=10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-budget", type=float, default=15.0)
+    p.add_argument("--ref-budget", type=float, default=120.0)
+    p.add_argument("--dims", type=lambda s: [int(x) for x in s.split(",")], default=list(DIMS),
+                   help="box for profiling runs (default 256,256,256: the workload)")
+    p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    args = p.parse_args(argv)
+    if args.warmup < 3:
+        p.error("--warmup must be >= 3")
+    world, _, _ = dist_setup()
+    if world != args.gpus and world > 1:
+        p.error(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * flbm.h - C ABI of the GB300 (sm_103a) fluctuating central-moment lattice Boltzmann
+ * library: the fused collide-and-stream step of De Rosis & Zhou, "A fluctuating
+ * lattice Boltzmann formulation based on orthogonal central moments" (arXiv:2602.16486),
+ * for D2Q9 and D3Q27 on periodic boxes.
+ *
+ * Conventions shared by every call
+ *  - Every function returns an int status (enum flbm_status); no C++ exception ever
+ *    crosses this boundary. On failure flbm_last_error() describes the cause.
+ *  - Out-pointers are written only when the call returns FLBM_OK (flbm_stats and
+ *    flbm_fetch_samples also write on FLBM_ENUMERIC, see there).
+ *  - The library owns everything it allocates. A device buffer or stream handed in by
+ *    the caller (flbm_create_ex) stays owned by the caller and must outlive the context.
+ *  - All device work of a context is issued on one CUDA stream (its own, or the
+ *    caller's). flbm_step and flbm_sample only enqueue work and never synchronise;
+ *    calls that return host data synchronise that stream.
+ *  - Populations cross the ABI in logical order, FP64, laid out [q][z][y][x] with x
+ *    fastest and q in the paper's velocity order (Sec. II-B for D2Q9, Sec. II-C for
+ *    D3Q27), whatever the storage type or the in-place streaming parity.
+ *  - Sites are numbered site = x + nx * (y + ny * z).
+ *  - A context is not thread safe: one host thread at a time may call into it.
+ */
+#ifndef FLBM_H
+#define FLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct flbm_ctx flbm_ctx;
+typedef struct flbm_batch flbm_batch;
+
+/* Lattices: D2Q9 (Sec. II-B) and D3Q27 (Sec. II-C). */
+enum flbm_lattice { FLBM_D2Q9 = 0, FLBM_D3Q27 = 1 };
+
+/* Storage of the deviations d_i = f_i - w_i * rho0 in device memory. All moment
+ * arithmetic is FP32 whatever the storage; statistics accumulate in FP64. */
+enum flbm_storage { FLBM_FP32 = 0, FLBM_BF16 = 1, FLBM_FP16 = 2 };
+
+enum flbm_status {
+  FLBM_OK = 0,
+  FLBM_EINVAL = 1,   /* invalid argument or handle                                   */
+  FLBM_ENOMEM = 2,   /* device or host allocation failed                             */
+  FLBM_ECUDA = 3,    /* a CUDA runtime call failed (message in flbm_last_error)       */
+  FLBM_ENUMERIC = 4, /* the sampled state holds non-finite values                     */
+  FLBM_ETIMEOUT = 5, /* a device-side bounded wait gave up (batched persistent kernel) */
+  FLBM_ESTATE = 6    /* call not valid in the current state (e.g. sample buffer full) */
+};
+
+/* Statistics of one state, taken before the collision of step `step` (the state
+ * after `step` completed steps). k_v are the central moments T(u(x)) f(x) of every
+ * site in the paper's mode order (Sec. II-B / II-C); means divide by `sites`.
+ * Entries beyond q (k_mean) or q*q (k_cov, row-major q x q) are zero. */
+typedef struct flbm_stats_t {
+  int64_t step;        /* completed steps when the sample was taken                */
+  int64_t sites;       /* nx * ny * nz                                              */
+  int64_t nonfinite;   /* sites whose rho, u or k is not finite (left out of sums)  */
+  int32_t lattice;     /* enum flbm_lattice                                         */
+  int32_t q;           /* 9 or 27                                                   */
+  double mass;         /* sum_x rho(x)                                              */
+  double mom[3];       /* sum_x rho u (x)                                           */
+  double u_mean[3];    /* <u_a>                                                     */
+  double uu[6];        /* <u_a u_b>: xx, yy, zz, xy, xz, yz                         */
+  double k_mean[27];   /* <k_v>                                                     */
+  double k_cov[27 * 27]; /* <k_v k_w> (raw second moments, symmetric)              */
+} flbm_stats_t;
+
+/* Bytes of device memory the populations of one lattice occupy (in-place streaming:
+ * one copy, Q * sites * sizeof(storage)). 0 for invalid arguments. */
+size_t flbm_required_bytes(int lattice, const int64_t dims[3], int storage);
+
+/*
+ * flbm_create - build a context for one periodic lattice at rest (f = f^eq(rho0, 0)).
+ *   lattice : FLBM_D2Q9 or FLBM_D3Q27.
+ *   dims    : {nx, ny, nz}, each >= 1; nz must be 1 for D2Q9; ny, nz <= 65535;
+ *             nx * ny * nz < 2^32 (the site index keys the noise).
+ *   lambda  : Q relaxation rates Lambda_v (Eq. cm_collision) in the paper's mode order;
+ *             entries of the conserved modes (v <= D) are ignored (forced to 1, as in
+ *             Sec. II-B and II-C); the others must lie in (0, 2].
+ *   kBT     : thermal energy per site, >= 0 (0 disables the noise; Test 1).
+ *   rho0    : reference density, > 0 (deviations are stored about w_i * rho0).
+ *   seed    : 64-bit key of the counter-based noise (see flbm_step).
+ * Storage FP32, a stream and device buffer owned by the library, current CUDA device.
+ */
+int flbm_create(flbm_ctx **out, int lattice, const int64_t dims[3], const double *lambda,
+                double kBT, double rho0, uint64_t seed);
+
+/*
+ * flbm_create_ex - as flbm_create, plus
+ *   storage     : enum flbm_storage.
+ *   cuda_stream : a cudaStream_t to issue all work on, or NULL for a library-owned
+ *                 non-blocking stream.
+ *   dev_buf     : device memory for the populations (>= flbm_required_bytes, 256-byte
+ *                 aligned), owned by the caller, or NULL to let the library allocate.
+ *   dev_buf_bytes : size of dev_buf in bytes (ignored when dev_buf is NULL).
+ */
+int flbm_create_ex(flbm_ctx **out, int lattice, const int64_t dims[3], const double *lambda,
+                   double kBT, double rho0, uint64_t seed, int storage, void *cuda_stream,
+                   void *dev_buf, size_t dev_buf_bytes);
+
+/* Release the context (synchronises its stream first). NULL is a no-op. */
+void flbm_destroy(flbm_ctx *ctx);
+
+/*
+ * flbm_init_uniform - reset to step 0 with f = f^eq(rho(x), u0) (the equilibrium of
+ * Sec. II-B / II-C, complete Hermite order), where
+ *   rho(x) = rho0 * (1 + rho_perturb_amp * (2 U(x) - 1)),
+ * U(x) the 23-bit uniform of word 0 of Philox4x32-10 at counter (site, 0, 0, 2^16)
+ * under key perturb_seed (the paper runs from rest with uniform rho0: amp = 0).
+ *   u0 : {ux, uy, uz} (uz ignored for D2Q9), |u0_a| < 1.
+ */
+int flbm_init_uniform(flbm_ctx *ctx, const double u0[3], double rho_perturb_amp,
+                      uint64_t perturb_seed);
+
+/*
+ * flbm_step - enqueue n >= 0 time steps of the fused collide-and-stream update
+ * (Sec. II-B "Algorithm of computation"; Eq. cm_collision with Eq. phi_general and the
+ * streaming Eq.), numbered step, step+1, ... from the context's current step count.
+ * Noise: for step s and site x the normals of the noisy modes v > D come from
+ * Philox4x32-10 (key = seed, counter = (site, s mod 2^32, s div 2^32, b)) with the
+ * Box-Muller transform: block b = (v - D - 1) / 4 gives four normals. Asynchronous;
+ * returns launch errors only.
+ */
+int flbm_step(flbm_ctx *ctx, int64_t n);
+
+/* Completed steps so far (the step index of the next update). -1 for a NULL ctx. */
+int64_t flbm_get_step(const flbm_ctx *ctx);
+
+/*
+ * flbm_stats - statistics of the current state (velocity moments, Sec. III Eq. for
+ * <u_a^2>; central-moment means and covariances, Sec. II-B C^eq), FP32 per site and
+ * FP64 accumulation. Synchronises. Returns FLBM_ENUMERIC (and still fills *out) when
+ * some site is not finite.
+ */
+int flbm_stats(flbm_ctx *ctx, flbm_stats_t *out);
+
+/*
+ * flbm_sample - enqueue the statistics of the current state into the next slot of the
+ * context's device-side sample buffer (asynchronous, no host synchronisation).
+ * FLBM_ESTATE when the buffer already holds flbm_sample_capacity() samples.
+ * flbm_fetch_samples - copy up to max_n recorded samples (oldest first) to out,
+ * set *n_out, and empty the buffer. Synchronises. FLBM_ENUMERIC if any fetched sample
+ * counted non-finite sites (out is still written).
+ * flbm_set_sample_capacity - (re)allocate the buffer for cap >= 1 samples; drops any
+ * recorded samples. The default capacity is 1024.
+ */
+int flbm_sample(flbm_ctx *ctx);
+int flbm_fetch_samples(flbm_ctx *ctx, flbm_stats_t *out, int max_n, int *n_out);
+int flbm_set_sample_capacity(flbm_ctx *ctx, int cap);
+int flbm_sample_capacity(const flbm_ctx *ctx);
+
+/* Logical populations f_i (FP64, [q][z][y][x]) of the whole lattice; count must equal
+ * Q * sites. Synchronises. */
+int flbm_get_populations(flbm_ctx *ctx, double *host, size_t count);
+int flbm_set_populations(flbm_ctx *ctx, const double *host, size_t count);
+
+/* Logical populations of n_sites chosen sites: out[s * Q + i] = f_i(sites[s]).
+ * Sites must lie in [0, nx*ny*nz). Synchronises. */
+int flbm_get_sites(flbm_ctx *ctx, const int64_t *sites, size_t n_sites, double *out);
+
+/*
+ * Checkpoint: a self-describing host blob (header + stored deviations in the context's
+ * storage type). flbm_load requires the same lattice, dims and storage and restores
+ * populations, step count, rates, kBT, rho0 and seed, so that "run a, save, load, run
+ * b" is bitwise equal to "run a + b". Both synchronise.
+ */
+size_t flbm_checkpoint_bytes(const flbm_ctx *ctx);
+int flbm_save(flbm_ctx *ctx, void *host, size_t bytes);
+int flbm_load(flbm_ctx *ctx, const void *host, size_t bytes);
+
+/* Wait for the context's stream. FLBM_ECUDA carries any asynchronous device error. */
+int flbm_sync(flbm_ctx *ctx);
+
+/* Message of the last failing call on this host thread (library-owned, never NULL). */
+const char *flbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLBM_H */

@@ -1,0 +1,545 @@
+// C ABI of the library (declared and documented in include/flbm.h): argument checks,
+// context ownership, launch sequencing and host <-> device exchange. Every compute
+// step runs in the kernels of step.cu, stats.cu and state.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/flbm.h"
+#include "internal.h"
+
+using namespace flbm;
+
+struct flbm_ctx {
+  int lattice = 0, D = 2, Q = 9, storage = 0;
+  int64_t dims[3] = {1, 1, 1};
+  long long N = 1;
+  double lambda[27] = {};
+  double kBT = 0.0, rho0 = 1.0;
+  uint64_t seed = 0;
+  int64_t step = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void *f = nullptr;
+  bool own_f = false;
+  size_t f_bytes = 0;
+  double *d_acc = nullptr;  // statistics accumulators (stats_record_len doubles)
+  double *h_acc = nullptr;  // pinned host mirror of d_acc
+  double *d_ring = nullptr;  // sample buffer: ring_cap records
+  int ring_cap = 0, ring_count = 0;
+  std::vector<int64_t> ring_steps;
+  double *d_stage = nullptr;  // FP64 staging for population exchange
+  size_t stage_elems = 0;
+  long long *d_sites = nullptr;
+  size_t sites_cap = 0;
+  StepArgs args{};
+};
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+int fail(int status, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return status;
+}
+
+#define FLBM_CUDA(call)                                                                   \
+  do {                                                                                    \
+    const cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) return fail(FLBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int q_of(int lattice) { return lattice == FLBM_D3Q27 ? 27 : 9; }
+int d_of(int lattice) { return lattice == FLBM_D3Q27 ? 3 : 2; }
+
+int check_geometry(int lattice, const int64_t dims[3], int storage) {
+  if (lattice != FLBM_D2Q9 && lattice != FLBM_D3Q27)
+    return fail(FLBM_EINVAL, "lattice must be FLBM_D2Q9 (0) or FLBM_D3Q27 (1), got %d", lattice);
+  if (!dims) return fail(FLBM_EINVAL, "dims is NULL");
+  for (int a = 0; a < 3; ++a)
+    if (dims[a] < 1) return fail(FLBM_EINVAL, "dims[%d] = %lld must be >= 1", a, (long long)dims[a]);
+  if (lattice == FLBM_D2Q9 && dims[2] != 1)
+    return fail(FLBM_EINVAL, "D2Q9 needs dims[2] (nz) == 1, got %lld", (long long)dims[2]);
+  if (dims[1] > 65535 || dims[2] > 65535)
+    return fail(FLBM_EINVAL, "ny and nz must be <= 65535");
+  if (dims[0] > 0x7fffffffLL) return fail(FLBM_EINVAL, "nx must be < 2^31");
+  const double n = double(dims[0]) * double(dims[1]) * double(dims[2]);
+  if (n >= 4294967296.0) return fail(FLBM_EINVAL, "nx*ny*nz must be < 2^32 (site index keys the noise)");
+  if (storage < FLBM_FP32 || storage > FLBM_FP16)
+    return fail(FLBM_EINVAL, "storage must be FLBM_FP32, FLBM_BF16 or FLBM_FP16, got %d", storage);
+  return FLBM_OK;
+}
+
+int check_params(int lattice, const double *lambda, double kBT, double rho0) {
+  if (!lambda) return fail(FLBM_EINVAL, "lambda is NULL");
+  const int Q = q_of(lattice), D = d_of(lattice);
+  for (int v = D + 1; v < Q; ++v)
+    if (!(lambda[v] > 0.0 && lambda[v] <= 2.0))
+      return fail(FLBM_EINVAL, "lambda[%d] = %g must lie in (0, 2]", v, lambda[v]);
+  if (!(kBT >= 0.0) || !std::isfinite(kBT)) return fail(FLBM_EINVAL, "kBT = %g must be finite and >= 0", kBT);
+  if (!(rho0 > 0.0) || !std::isfinite(rho0)) return fail(FLBM_EINVAL, "rho0 = %g must be finite and > 0", rho0);
+  return FLBM_OK;
+}
+
+// Per-mode constants of the collision: om_v = 1 - L_v and
+// phc_v = sqrt(kBT L_v (2 - L_v) b_v / cs^2) (Eq. phi_general without the sqrt(rho)).
+void fill_args(flbm_ctx *c) {
+  StepArgs &a = c->args;
+  a.f = c->f;
+  a.plane = c->N;
+  a.nx = int(c->dims[0]);
+  a.ny = int(c->dims[1]);
+  a.nz = int(c->dims[2]);
+  a.rho0 = float(c->rho0);
+  a.key0 = uint32_t(c->seed);
+  a.key1 = uint32_t(c->seed >> 32);
+  for (int v = 0; v < 27; ++v) {
+    a.om[v] = 0.0f;
+    a.phc[v] = 0.0f;
+  }
+  for (int v = c->D + 1; v < c->Q; ++v) {
+    const double L = c->lambda[v];
+    a.om[v] = float(1.0 - L);
+    a.phc[v] = float(std::sqrt(c->kBT * L * (2.0 - L) * mode_bnorm(c->D, v) * 3.0));
+  }
+}
+
+void release(flbm_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->own_f && c->f) cudaFree(c->f);
+  if (c->d_acc) cudaFree(c->d_acc);
+  if (c->h_acc) cudaFreeHost(c->h_acc);
+  if (c->d_ring) cudaFree(c->d_ring);
+  if (c->d_stage) cudaFree(c->d_stage);
+  if (c->d_sites) cudaFree(c->d_sites);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int ensure_stage(flbm_ctx *c, size_t elems) {
+  if (c->stage_elems >= elems) return FLBM_OK;
+  if (c->d_stage) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->stage_elems = 0;
+  }
+  if (cudaMalloc(&c->d_stage, elems * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FLBM_ENOMEM, "cannot allocate %zu bytes of staging memory", elems * sizeof(double));
+  }
+  c->stage_elems = elems;
+  return FLBM_OK;
+}
+
+// Host struct from one record of accumulators (layout in stats.cu).
+void fill_stats(const flbm_ctx *c, const double *acc, int64_t step, flbm_stats_t *out) {
+  const int Q = c->Q;
+  const int nacc = stats_nacc(Q);
+  std::memset(out, 0, sizeof(*out));
+  out->step = step;
+  out->sites = c->N;
+  out->lattice = c->lattice;
+  out->q = Q;
+  out->nonfinite = (int64_t)llround(acc[nacc]);
+  const double inv = 1.0 / double(c->N);
+  out->mass = c->rho0 * acc[0] + acc[1];
+  for (int a = 0; a < 3; ++a) {
+    out->mom[a] = acc[2 + a];
+    out->u_mean[a] = acc[5 + a] * inv;
+  }
+  for (int a = 0; a < 6; ++a) out->uu[a] = acc[8 + a] * inv;
+  for (int v = 0; v < Q; ++v) out->k_mean[v] = acc[14 + v] * inv;
+  int e = 14 + Q;
+  for (int v = 0; v < Q; ++v)
+    for (int w = v; w < Q; ++w, ++e) {
+      out->k_cov[v * Q + w] = acc[e] * inv;
+      out->k_cov[w * Q + v] = acc[e] * inv;
+    }
+}
+
+int enqueue_stats(flbm_ctx *c, double *acc_dev) {
+  FLBM_CUDA(cudaMemsetAsync(acc_dev, 0, sizeof(double) * stats_record_len(c->Q), c->stream));
+  FLBM_CUDA(launch_stats(c->D, c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
+                         int(c->dims[1]), int(c->dims[2]), float(c->rho0), acc_dev, c->stream));
+  return FLBM_OK;
+}
+
+struct CkptHeader {
+  char magic[8];
+  int32_t version, lattice, storage, q;
+  int64_t dims[3];
+  int64_t step;
+  uint64_t seed;
+  double kBT, rho0;
+  double lambda[27];
+  uint64_t payload_bytes;
+};
+const char kMagic[8] = {'F', 'L', 'B', 'M', 'C', 'K', 'P', '1'};
+
+}  // namespace
+
+extern "C" {
+
+size_t flbm_required_bytes(int lattice, const int64_t dims[3], int storage) {
+  const std::string saved = g_last_error;
+  if (check_geometry(lattice, dims, storage) != FLBM_OK) return 0;
+  g_last_error = saved;
+  return size_t(q_of(lattice)) * size_t(dims[0] * dims[1] * dims[2]) * storage_bytes(storage);
+}
+
+int flbm_create_ex(flbm_ctx **out, int lattice, const int64_t dims[3], const double *lambda,
+                   double kBT, double rho0, uint64_t seed, int storage, void *cuda_stream,
+                   void *dev_buf, size_t dev_buf_bytes) {
+  if (!out) return fail(FLBM_EINVAL, "out is NULL");
+  int st = check_geometry(lattice, dims, storage);
+  if (st != FLBM_OK) return st;
+  st = check_params(lattice, lambda, kBT, rho0);
+  if (st != FLBM_OK) return st;
+  const size_t need = flbm_required_bytes(lattice, dims, storage);
+  if (dev_buf) {
+    if (dev_buf_bytes < need)
+      return fail(FLBM_EINVAL, "dev_buf holds %zu bytes, %zu needed", dev_buf_bytes, need);
+    if (reinterpret_cast<uintptr_t>(dev_buf) % 256 != 0)
+      return fail(FLBM_EINVAL, "dev_buf must be 256-byte aligned");
+  }
+  int dev = 0;
+  FLBM_CUDA(cudaGetDevice(&dev));
+
+  flbm_ctx *c = new (std::nothrow) flbm_ctx();
+  if (!c) return fail(FLBM_ENOMEM, "host allocation failed");
+  c->lattice = lattice;
+  c->D = d_of(lattice);
+  c->Q = q_of(lattice);
+  c->storage = storage;
+  for (int a = 0; a < 3; ++a) c->dims[a] = dims[a];
+  c->N = (long long)(dims[0] * dims[1] * dims[2]);
+  for (int v = 0; v < c->Q; ++v) c->lambda[v] = (v <= c->D) ? 1.0 : lambda[v];
+  c->kBT = kBT;
+  c->rho0 = rho0;
+  c->seed = seed;
+  c->device = dev;
+  c->f_bytes = need;
+
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      release(c);
+      return fail(FLBM_ECUDA, "cudaStreamCreateWithFlags: %s", cudaGetErrorString(e));
+    }
+    c->own_stream = true;
+  }
+  if (dev_buf) {
+    c->f = dev_buf;
+  } else {
+    e = cudaMalloc(&c->f, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->f = nullptr;
+      release(c);
+      return fail(FLBM_ENOMEM, "cannot allocate %zu bytes of population memory", need);
+    }
+    c->own_f = true;
+  }
+  const size_t acc_bytes = sizeof(double) * stats_record_len(c->Q);
+  e = cudaMalloc(&c->d_acc, acc_bytes);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_acc, acc_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release(c);
+    return fail(FLBM_ENOMEM, "cannot allocate statistics buffers");
+  }
+  fill_args(c);
+  // Rest state f = w rho0: every stored deviation is zero (also for BF16/FP16 bits).
+  e = cudaMemsetAsync(c->f, 0, need, c->stream);
+  if (e != cudaSuccess) {
+    release(c);
+    return fail(FLBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return FLBM_OK;
+}
+
+int flbm_create(flbm_ctx **out, int lattice, const int64_t dims[3], const double *lambda,
+                double kBT, double rho0, uint64_t seed) {
+  return flbm_create_ex(out, lattice, dims, lambda, kBT, rho0, seed, FLBM_FP32, nullptr, nullptr, 0);
+}
+
+void flbm_destroy(flbm_ctx *ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  release(ctx);
+}
+
+int flbm_init_uniform(flbm_ctx *c, const double u0[3], double amp, uint64_t perturb_seed) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (!u0) return fail(FLBM_EINVAL, "u0 is NULL");
+  for (int a = 0; a < c->D; ++a)
+    if (!(std::fabs(u0[a]) < 1.0)) return fail(FLBM_EINVAL, "|u0[%d]| = %g must be < 1", a, u0[a]);
+  if (!(amp >= 0.0 && amp < 1.0)) return fail(FLBM_EINVAL, "rho_perturb_amp = %g must lie in [0, 1)", amp);
+  DeviceGuard g(c->device);
+  FLBM_CUDA(launch_init(c->D, c->storage, c->f, c->N, int(c->dims[0]), int(c->dims[1]),
+                        int(c->dims[2]), c->rho0, u0[0], u0[1], c->D == 3 ? u0[2] : 0.0, amp,
+                        perturb_seed, c->stream));
+  c->step = 0;
+  return FLBM_OK;
+}
+
+int flbm_step(flbm_ctx *c, int64_t n) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (n < 0) return fail(FLBM_EINVAL, "n = %lld must be >= 0", (long long)n);
+  DeviceGuard g(c->device);
+  const bool noise = c->kBT > 0.0;
+  for (int64_t s = 0; s < n; ++s) {
+    c->args.step_lo = uint32_t(uint64_t(c->step));
+    c->args.step_hi = uint32_t(uint64_t(c->step) >> 32);
+    FLBM_CUDA(launch_step(c->D, c->storage, int(c->step & 1), noise, c->args, c->stream));
+    ++c->step;
+  }
+  return FLBM_OK;
+}
+
+int64_t flbm_get_step(const flbm_ctx *c) { return c ? c->step : -1; }
+
+int flbm_stats(flbm_ctx *c, flbm_stats_t *out) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (!out) return fail(FLBM_EINVAL, "out is NULL");
+  DeviceGuard g(c->device);
+  int st = enqueue_stats(c, c->d_acc);
+  if (st != FLBM_OK) return st;
+  FLBM_CUDA(cudaMemcpyAsync(c->h_acc, c->d_acc, sizeof(double) * stats_record_len(c->Q),
+                            cudaMemcpyDeviceToHost, c->stream));
+  FLBM_CUDA(cudaStreamSynchronize(c->stream));
+  fill_stats(c, c->h_acc, c->step, out);
+  if (out->nonfinite > 0)
+    return fail(FLBM_ENUMERIC, "%lld sites hold non-finite values at step %lld",
+                (long long)out->nonfinite, (long long)c->step);
+  return FLBM_OK;
+}
+
+int flbm_set_sample_capacity(flbm_ctx *c, int cap) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (cap < 1) return fail(FLBM_EINVAL, "capacity must be >= 1");
+  DeviceGuard g(c->device);
+  FLBM_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->d_ring) cudaFree(c->d_ring);
+  c->d_ring = nullptr;
+  c->ring_cap = c->ring_count = 0;
+  c->ring_steps.clear();
+  if (cudaMalloc(&c->d_ring, sizeof(double) * size_t(stats_record_len(c->Q)) * size_t(cap)) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_ring = nullptr;
+    return fail(FLBM_ENOMEM, "cannot allocate a sample buffer of %d records", cap);
+  }
+  c->ring_cap = cap;
+  return FLBM_OK;
+}
+
+int flbm_sample_capacity(const flbm_ctx *c) { return c ? (c->d_ring ? c->ring_cap : 1024) : -1; }
+
+int flbm_sample(flbm_ctx *c) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (!c->d_ring) {
+    const int st = flbm_set_sample_capacity(c, 1024);
+    if (st != FLBM_OK) return st;
+  }
+  if (c->ring_count >= c->ring_cap)
+    return fail(FLBM_ESTATE, "sample buffer full (%d samples); fetch first", c->ring_cap);
+  DeviceGuard g(c->device);
+  double *slot = c->d_ring + size_t(c->ring_count) * size_t(stats_record_len(c->Q));
+  const int st = enqueue_stats(c, slot);
+  if (st != FLBM_OK) return st;
+  c->ring_steps.push_back(c->step);
+  ++c->ring_count;
+  return FLBM_OK;
+}
+
+int flbm_fetch_samples(flbm_ctx *c, flbm_stats_t *out, int max_n, int *n_out) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (!n_out || (!out && max_n > 0) || max_n < 0) return fail(FLBM_EINVAL, "bad output arguments");
+  DeviceGuard g(c->device);
+  const int n = c->ring_count < max_n ? c->ring_count : max_n;
+  const size_t len = size_t(stats_record_len(c->Q));
+  std::vector<double> h(len * size_t(n > 0 ? n : 1));
+  if (n > 0)
+    FLBM_CUDA(cudaMemcpyAsync(h.data(), c->d_ring, sizeof(double) * len * size_t(n),
+                              cudaMemcpyDeviceToHost, c->stream));
+  FLBM_CUDA(cudaStreamSynchronize(c->stream));
+  int64_t bad = 0;
+  for (int k = 0; k < n; ++k) {
+    fill_stats(c, h.data() + len * size_t(k), c->ring_steps[size_t(k)], &out[k]);
+    bad += out[k].nonfinite;
+  }
+  c->ring_count = 0;
+  c->ring_steps.clear();
+  *n_out = n;
+  if (bad > 0) return fail(FLBM_ENUMERIC, "fetched samples count %lld non-finite sites", (long long)bad);
+  return FLBM_OK;
+}
+
+int flbm_get_populations(flbm_ctx *c, double *host, size_t count) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (!host) return fail(FLBM_EINVAL, "host is NULL");
+  if (count != size_t(c->Q) * size_t(c->N))
+    return fail(FLBM_EINVAL, "count = %zu, expected Q * sites = %zu", count, size_t(c->Q) * size_t(c->N));
+  DeviceGuard g(c->device);
+  int st = ensure_stage(c, size_t(c->N));
+  if (st != FLBM_OK) return st;
+  for (int q = 0; q < c->Q; ++q) {
+    FLBM_CUDA(launch_gather_plane(c->D, c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
+                                  int(c->dims[1]), int(c->dims[2]), c->rho0, q, c->d_stage, c->stream));
+    FLBM_CUDA(cudaMemcpyAsync(host + size_t(q) * size_t(c->N), c->d_stage, sizeof(double) * size_t(c->N),
+                              cudaMemcpyDeviceToHost, c->stream));
+    FLBM_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return FLBM_OK;
+}
+
+int flbm_set_populations(flbm_ctx *c, const double *host, size_t count) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (!host) return fail(FLBM_EINVAL, "host is NULL");
+  if (count != size_t(c->Q) * size_t(c->N))
+    return fail(FLBM_EINVAL, "count = %zu, expected Q * sites = %zu", count, size_t(c->Q) * size_t(c->N));
+  DeviceGuard g(c->device);
+  int st = ensure_stage(c, size_t(c->N));
+  if (st != FLBM_OK) return st;
+  for (int q = 0; q < c->Q; ++q) {
+    FLBM_CUDA(cudaMemcpyAsync(c->d_stage, host + size_t(q) * size_t(c->N), sizeof(double) * size_t(c->N),
+                              cudaMemcpyHostToDevice, c->stream));
+    FLBM_CUDA(launch_scatter_plane(c->D, c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
+                                   int(c->dims[1]), int(c->dims[2]), c->rho0, q, c->d_stage, c->stream));
+  }
+  FLBM_CUDA(cudaStreamSynchronize(c->stream));
+  return FLBM_OK;
+}
+
+int flbm_get_sites(flbm_ctx *c, const int64_t *sites, size_t n, double *out) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (n == 0) return FLBM_OK;
+  if (!sites || !out) return fail(FLBM_EINVAL, "sites or out is NULL");
+  for (size_t k = 0; k < n; ++k)
+    if (sites[k] < 0 || sites[k] >= c->N)
+      return fail(FLBM_EINVAL, "sites[%zu] = %lld out of range [0, %lld)", k, (long long)sites[k], c->N);
+  DeviceGuard g(c->device);
+  if (c->sites_cap < n) {
+    FLBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->d_sites) cudaFree(c->d_sites);
+    c->d_sites = nullptr;
+    c->sites_cap = 0;
+    if (cudaMalloc(&c->d_sites, n * sizeof(long long)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FLBM_ENOMEM, "cannot allocate the site list");
+    }
+    c->sites_cap = n;
+  }
+  int st = ensure_stage(c, n * size_t(c->Q));
+  if (st != FLBM_OK) return st;
+  static_assert(sizeof(long long) == sizeof(int64_t), "site index width");
+  FLBM_CUDA(cudaMemcpyAsync(c->d_sites, sites, n * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+  FLBM_CUDA(launch_gather_sites(c->D, c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
+                                int(c->dims[1]), int(c->dims[2]), c->rho0, c->d_sites, (long long)n,
+                                c->d_stage, c->stream));
+  FLBM_CUDA(cudaMemcpyAsync(out, c->d_stage, n * size_t(c->Q) * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+  FLBM_CUDA(cudaStreamSynchronize(c->stream));
+  return FLBM_OK;
+}
+
+size_t flbm_checkpoint_bytes(const flbm_ctx *c) { return c ? sizeof(CkptHeader) + c->f_bytes : 0; }
+
+int flbm_save(flbm_ctx *c, void *host, size_t bytes) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (!host) return fail(FLBM_EINVAL, "host is NULL");
+  if (bytes < flbm_checkpoint_bytes(c))
+    return fail(FLBM_EINVAL, "checkpoint needs %zu bytes, got %zu", flbm_checkpoint_bytes(c), bytes);
+  DeviceGuard g(c->device);
+  CkptHeader h{};
+  std::memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.lattice = c->lattice;
+  h.storage = c->storage;
+  h.q = c->Q;
+  for (int a = 0; a < 3; ++a) h.dims[a] = c->dims[a];
+  h.step = c->step;
+  h.seed = c->seed;
+  h.kBT = c->kBT;
+  h.rho0 = c->rho0;
+  for (int v = 0; v < 27; ++v) h.lambda[v] = c->lambda[v];
+  h.payload_bytes = c->f_bytes;
+  std::memcpy(host, &h, sizeof(h));
+  FLBM_CUDA(cudaMemcpyAsync(static_cast<char *>(host) + sizeof(h), c->f, c->f_bytes,
+                            cudaMemcpyDeviceToHost, c->stream));
+  FLBM_CUDA(cudaStreamSynchronize(c->stream));
+  return FLBM_OK;
+}
+
+int flbm_load(flbm_ctx *c, const void *host, size_t bytes) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (!host) return fail(FLBM_EINVAL, "host is NULL");
+  if (bytes < sizeof(CkptHeader)) return fail(FLBM_EINVAL, "blob too small for a checkpoint header");
+  CkptHeader h;
+  std::memcpy(&h, host, sizeof(h));
+  if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) return fail(FLBM_EINVAL, "not a checkpoint blob");
+  if (h.lattice != c->lattice || h.storage != c->storage || h.dims[0] != c->dims[0] ||
+      h.dims[1] != c->dims[1] || h.dims[2] != c->dims[2] || h.payload_bytes != c->f_bytes)
+    return fail(FLBM_EINVAL, "checkpoint lattice, dims or storage differ from the context");
+  if (bytes < sizeof(h) + h.payload_bytes) return fail(FLBM_EINVAL, "checkpoint blob truncated");
+  const int st = check_params(h.lattice, h.lambda, h.kBT, h.rho0);
+  if (st != FLBM_OK) return st;
+  DeviceGuard g(c->device);
+  FLBM_CUDA(cudaMemcpyAsync(c->f, static_cast<const char *>(host) + sizeof(h), c->f_bytes,
+                            cudaMemcpyHostToDevice, c->stream));
+  FLBM_CUDA(cudaStreamSynchronize(c->stream));
+  c->step = h.step;
+  c->seed = h.seed;
+  c->kBT = h.kBT;
+  c->rho0 = h.rho0;
+  for (int v = 0; v < c->Q; ++v) c->lambda[v] = (v <= c->D) ? 1.0 : h.lambda[v];
+  fill_args(c);
+  return FLBM_OK;
+}
+
+int flbm_sync(flbm_ctx *c) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  DeviceGuard g(c->device);
+  FLBM_CUDA(cudaStreamSynchronize(c->stream));
+  return FLBM_OK;
+}
+
+const char *flbm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

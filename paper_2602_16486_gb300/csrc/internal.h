@@ -1,0 +1,54 @@
+// Host-side internals shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace flbm {
+
+constexpr int kStepBlock = 128;   // threads per block of the step kernels (x direction)
+constexpr int kStatsBlock = 128;  // threads (= sites per tile) of the statistics kernel
+
+// Arguments of one fused step launch (passed by value, lives in the constant bank).
+struct StepArgs {
+  void *f;            // populations (deviations), Q planes of `plane` elements
+  long long plane;    // nx * ny * nz
+  int nx, ny, nz;
+  float rho0;
+  uint32_t key0, key1;        // noise key (seed)
+  uint32_t step_lo, step_hi;  // step number of this update
+  float om[27];       // 1 - Lambda_v (conserved modes: unused)
+  float phc[27];      // sqrt(kBT Lambda_v (2 - Lambda_v) b_v / cs^2); phi_v = sqrt(rho) phc_v
+};
+
+// Statistics accumulators, in doubles: see stats.cu for the layout.
+int stats_nacc(int Q);
+inline int stats_record_len(int Q) { return stats_nacc(Q) + 1; }  // + non-finite count
+
+cudaError_t launch_step(int D, int storage, int parity, bool noise, const StepArgs &a,
+                        cudaStream_t s);
+cudaError_t launch_stats(int D, int storage, int parity, const void *f, long long plane, int nx,
+                         int ny, int nz, float rho0, double *acc, cudaStream_t s);
+cudaError_t launch_init(int D, int storage, void *f, long long plane, int nx, int ny, int nz,
+                        double rho0, double ux, double uy, double uz, double amp,
+                        uint64_t perturb_seed, cudaStream_t s);
+cudaError_t launch_gather_plane(int D, int storage, int parity, const void *f, long long plane,
+                                int nx, int ny, int nz, double rho0, int q, double *out,
+                                cudaStream_t s);
+cudaError_t launch_scatter_plane(int D, int storage, int parity, void *f, long long plane, int nx,
+                                 int ny, int nz, double rho0, int q, const double *in,
+                                 cudaStream_t s);
+cudaError_t launch_gather_sites(int D, int storage, int parity, const void *f, long long plane,
+                                int nx, int ny, int nz, double rho0, const long long *sites,
+                                long long n, double *out, cudaStream_t s);
+
+// Modal norms b_v of the device bases (host copy, computed from the same tensor
+// structure the kernels use) and the storage element size.
+double mode_bnorm(int D, int v);
+size_t storage_bytes(int storage);
+
+}  // namespace flbm
