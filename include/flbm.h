@@ -171,6 +171,35 @@ size_t flbm_checkpoint_bytes(const flbm_ctx *ctx);
 int flbm_save(flbm_ctx *ctx, void *host, size_t bytes);
 int flbm_load(flbm_ctx *ctx, const void *host, size_t bytes);
 
+/*
+ * flbm_stats_noalloc - the statistics of flbm_stats (same kernel, same flbm_stats_t)
+ * for a population array the caller owns, with no allocation of any kind. The paper
+ * has no counterpart: this entry point exists for callers that cannot allocate GPU
+ * memory - code that owns the whole device-memory budget through its own pool, code
+ * that must not change its memory footprint once running, or code inside a CUDA stream
+ * capture, where cudaMalloc is not allowed. flbm_create cannot serve them, because it
+ * allocates its buffers.
+ *   lattice, dims, storage, rho0 : as given to flbm_create_ex for this array.
+ *   parity          : completed steps mod 2 (flbm_get_step(ctx) & 1): 0 when the array
+ *                     holds f_i(x) in slot i at x, 1 after an odd number of AA steps.
+ *   dev_populations : the stored deviations, device memory, Q * sites elements of the
+ *                     storage type (e.g. the dev_buf handed to flbm_create_ex).
+ *   cuda_stream     : stream to run on (NULL = legacy default stream); synchronised.
+ *   out             : host struct, written on FLBM_OK and FLBM_ENUMERIC; out->step is
+ *                     -1 (the array carries no step count).
+ * Scratch: the FP64 accumulators live in one statically allocated device array of
+ * FLBM_NOALLOC_SCRATCH_DOUBLES doubles (4 KiB), which every GPU that loads the library
+ * keeps until the process exits. A lattice whose accumulators would not fit is rejected
+ * with FLBM_EINVAL (D2Q9 needs 69 doubles, D3Q27 420). The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) and caches it; make that first
+ * call before any stream capture. Every call reuses the same array and zeroes it first,
+ * so calls whose GPU work overlaps (other streams, other host threads) race and return
+ * wrong sums: serialise them.
+ */
+#define FLBM_NOALLOC_SCRATCH_DOUBLES 512
+int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storage, int parity, double rho0,
+                       const void *dev_populations, void *cuda_stream, flbm_stats_t *out);
+
 /* Wait for the context's stream. FLBM_ECUDA carries any asynchronous device error. */
 int flbm_sync(flbm_ctx *ctx);
 

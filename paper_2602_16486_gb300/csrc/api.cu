@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -543,3 +544,75 @@ int flbm_sync(flbm_ctx *c) {
 const char *flbm_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---- statistics without allocation -----------------------------------------------------
+// Scratch of flbm_stats_noalloc: the accumulators of the statistics kernel in a fixed
+// device array, so that the call needs no cudaMalloc. Host code may not use the array's
+// name as an address; its device address is looked up once per device.
+namespace {
+
+static __device__ __align__(256) double g_noalloc_scratch[FLBM_NOALLOC_SCRATCH_DOUBLES];
+
+constexpr int kNoallocMaxDevices = 64;
+double *g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch on the current device (first use: symbol lookup).
+int noalloc_scratch(double **out) {
+  int dev = 0;
+  FLBM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices)
+    return fail(FLBM_EINVAL, "device %d beyond the %d devices flbm_stats_noalloc supports", dev,
+                kNoallocMaxDevices);
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(FLBM_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return FLBM_OK;
+}
+
+}  // namespace
+
+extern "C" int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storage, int parity,
+                                  double rho0, const void *dev_populations, void *cuda_stream,
+                                  flbm_stats_t *out) {
+  int st = check_geometry(lattice, dims, storage);
+  if (st != FLBM_OK) return st;
+  if (parity != 0 && parity != 1) return fail(FLBM_EINVAL, "parity must be 0 or 1, got %d", parity);
+  if (!(rho0 > 0.0) || !std::isfinite(rho0)) return fail(FLBM_EINVAL, "rho0 = %g must be finite and > 0", rho0);
+  if (!dev_populations) return fail(FLBM_EINVAL, "dev_populations is NULL");
+  if (reinterpret_cast<uintptr_t>(dev_populations) % storage_bytes(storage) != 0)
+    return fail(FLBM_EINVAL, "dev_populations is not aligned to its element size");
+  if (!out) return fail(FLBM_EINVAL, "out is NULL");
+  const int Q = q_of(lattice);
+  const int len = stats_record_len(Q);
+  if (len > FLBM_NOALLOC_SCRATCH_DOUBLES)
+    return fail(FLBM_EINVAL, "the statistics need %d doubles of scratch; the static scratch holds %d",
+                len, FLBM_NOALLOC_SCRATCH_DOUBLES);
+  double *acc = nullptr;
+  st = noalloc_scratch(&acc);
+  if (st != FLBM_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const long long N = (long long)(dims[0] * dims[1] * dims[2]);
+  FLBM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * size_t(len), s));
+  FLBM_CUDA(launch_stats(d_of(lattice), storage, parity, dev_populations, N, int(dims[0]), int(dims[1]),
+                         int(dims[2]), float(rho0), acc, s));
+  double h[FLBM_NOALLOC_SCRATCH_DOUBLES];
+  FLBM_CUDA(cudaMemcpyAsync(h, acc, sizeof(double) * size_t(len), cudaMemcpyDeviceToHost, s));
+  FLBM_CUDA(cudaStreamSynchronize(s));
+  // The host conversion of flbm_stats, fed with a description of this array.
+  flbm_ctx view;
+  view.lattice = lattice;
+  view.Q = Q;
+  view.N = N;
+  view.rho0 = rho0;
+  fill_stats(&view, h, -1, out);
+  if (out->nonfinite > 0)
+    return fail(FLBM_ENUMERIC, "%lld sites hold non-finite values", (long long)out->nonfinite);
+  return FLBM_OK;
+}

@@ -89,6 +89,8 @@ def _load():
         "flbm_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
         "flbm_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
         "flbm_sync": (ctypes.c_int, [vp]),
+        "flbm_stats_noalloc": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_double, vp, vp, ctypes.POINTER(flbm_stats_t)]),
         "flbm_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -244,6 +246,20 @@ def flbm_load(ctx, blob=None, host_ptr=None, nbytes=None):
 
 def flbm_sync(ctx):
     _check(_lib.flbm_sync(ctx))
+
+
+def flbm_stats_noalloc(lattice, dims, storage, parity, rho0, dev_populations, cuda_stream=None,
+                       allow_nonfinite=False):
+    """Statistics of a caller-owned device population array; the library allocates
+    nothing for this call (see include/flbm.h)."""
+    out = flbm_stats_t()
+    st = _lib.flbm_stats_noalloc(int(lattice), _dims(dims), int(storage), int(parity), float(rho0),
+                                 ctypes.c_void_p(dev_populations),
+                                 ctypes.c_void_p(cuda_stream) if cuda_stream else None,
+                                 ctypes.byref(out))
+    if not (st == FLBM_ENUMERIC and allow_nonfinite):
+        _check(st)
+    return out.to_dict()
 
 
 def flbm_last_error():
