@@ -187,6 +187,11 @@ def run_ours(args):
                      cuda_stream=stream.cuda_stream)
     fl.flbm_set_sample_capacity(lat.ctx, max(1, (args.steps + args.warmup) // S + 2))
     lat.init_uniform(U0, AMP, SEED + rank)
+    if args.variant:
+        lat.variant = args.variant
+        variant = lat.variant
+    else:
+        variant = lat.autotune(10)  # launch configuration only; runs on a copy of the state
 
     def one_step(k):
         lat.step(1)
@@ -281,7 +286,7 @@ def run_ours(args):
         "unit": "GB/s",
         "frac": round(achieved / peaks["hbm_gbs"], 4),
         "traffic": recorded_traffic(),
-        "kernel": "step_kernel<D3Q27, fp32> (fused collide + AA stream)",
+        "kernel": f"fused collide + AA stream, D3Q27 fp32 (step variant {variant})",
         "peak_kind": f"{peak_kind} STREAM-style copy (hbm_gbs)",
         "algorithmic_bytes_per_launch": BYTES_PER_SITE * sites,
         "avg_launch_ms": round(avg_kernel_ms, 5),
@@ -299,7 +304,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded lattice state, no dataset)",
-        "config": workload_config(S, world, dims),
+        "config": dict(workload_config(S, world, dims), step_variant=variant),
         "roofline": roof,
         "e2e": {
             "value": round(world * sites * n_e2e / e2e_s / 1e9, 3),
@@ -415,6 +420,8 @@ def main(argv=None):
     p.add_argument("--dims", type=lambda s: [int(x) for x in s.split(",")], default=list(DIMS),
                    help="box for profiling runs (default 256,256,256: the workload)")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    p.add_argument("--variant", type=int, default=0,
+                   help="step-kernel variant (1-4); default 0 = autotune")
     args = p.parse_args(argv)
     if args.warmup < 3:
         p.error("--warmup must be >= 3")

@@ -200,6 +200,25 @@ int flbm_load(flbm_ctx *ctx, const void *host, size_t bytes);
 int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storage, int parity, double rho0,
                        const void *dev_populations, void *cuda_stream, flbm_stats_t *out);
 
+/*
+ * Step-kernel variant (launch configuration only; every variant computes the same
+ * update): 0 = default (2 when nx is even, else 1), 1 = one site per thread, 2 = two
+ * sites per thread, 3 = two sites per thread with the noise generated in a rolled loop
+ * (smaller code), 4 = a persistent kernel that prefetches each row's populations into
+ * shared memory with bulk asynchronous copies (needs nx even, nx <= 512 and a
+ * population row a multiple of 16 bytes; else it falls back to 2). Variants 2-4 fall
+ * back to 1 when nx is odd. The environment variable FLBM_STEP_VARIANT, read by
+ * flbm_create, sets the initial choice.
+ * flbm_autotune times every applicable variant over trial_steps steps on a copy of the
+ * current state (restored afterwards: populations and step count are unchanged), keeps
+ * the fastest for this context and caches the choice per (GPU model, lattice, storage,
+ * nx parity, size class, noise on/off) for the process. Needs one extra copy of the
+ * populations in device memory while it runs. Synchronises.
+ */
+int flbm_set_step_variant(flbm_ctx *ctx, int variant);
+int flbm_get_step_variant(const flbm_ctx *ctx);
+int flbm_autotune(flbm_ctx *ctx, int trial_steps, int *chosen);
+
 /* Wait for the context's stream. FLBM_ECUDA carries any asynchronous device error. */
 int flbm_sync(flbm_ctx *ctx);
 

@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -40,6 +42,9 @@ struct flbm_ctx {
   size_t stage_elems = 0;
   long long *d_sites = nullptr;
   size_t sites_cap = 0;
+  int variant = 0;  // enum StepVariant; 0 = default choice
+  bool shear = false;  // rates follow the paper's structure (collide.cuh, SHEAR)
+  int *d_status = nullptr;  // device status word of the pipelined kernel
   StepArgs args{};
 };
 
@@ -122,8 +127,13 @@ void fill_args(flbm_ctx *c) {
   a.ny = int(c->dims[1]);
   a.nz = int(c->dims[2]);
   a.rho0 = float(c->rho0);
+  a.status = c->d_status;
   a.key0 = uint32_t(c->seed);
   a.key1 = uint32_t(c->seed >> 32);
+  for (int r = 0; r < 10; ++r) {  // Weyl key schedule of Philox4x32 (Salmon et al., SC'11)
+    a.ks0[r] = a.key0 + uint32_t(r) * 0x9E3779B9u;
+    a.ks1[r] = a.key1 + uint32_t(r) * 0xBB67AE85u;
+  }
   for (int v = 0; v < 27; ++v) {
     a.om[v] = 0.0f;
     a.phc[v] = 0.0f;
@@ -132,6 +142,12 @@ void fill_args(flbm_ctx *c) {
     const double L = c->lambda[v];
     a.om[v] = float(1.0 - L);
     a.phc[v] = float(std::sqrt(c->kBT * L * (2.0 - L) * mode_bnorm(c->D, v) * 3.0));
+  }
+  // The paper's structure: rate 1 for every non-conserved mode except the shear modes.
+  c->shear = true;
+  for (int v = c->D + 1; v < c->Q; ++v) {
+    const bool is_shear = (c->D == 3) ? (v >= 7 && v <= 9) : (v == 4 || v == 5);
+    if (!is_shear && c->lambda[v] != 1.0) c->shear = false;
   }
 }
 
@@ -144,6 +160,7 @@ void release(flbm_ctx *c) {
   if (c->d_ring) cudaFree(c->d_ring);
   if (c->d_stage) cudaFree(c->d_stage);
   if (c->d_sites) cudaFree(c->d_sites);
+  if (c->d_status) cudaFree(c->d_status);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -194,6 +211,29 @@ int enqueue_stats(flbm_ctx *c, double *acc_dev) {
   FLBM_CUDA(cudaMemsetAsync(acc_dev, 0, sizeof(double) * stats_record_len(c->Q), c->stream));
   FLBM_CUDA(launch_stats(c->D, c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
                          int(c->dims[1]), int(c->dims[2]), float(c->rho0), acc_dev, c->stream));
+  return FLBM_OK;
+}
+
+// Variant actually launched: the choice, or the default (two sites per thread where nx
+// is even, else one site per thread); the pipelined choice falls back where it does not
+// apply.
+int resolve_variant(const flbm_ctx *c) {
+  const bool pipe = pipe_applicable(c->D, c->storage, int(c->dims[0]));
+  int v = c->variant;
+  if (v == kStepAuto) v = kStepPair;
+  if (v == kStepPipelined && !pipe) v = kStepPair;
+  if (v != kStepOneSite && c->dims[0] % 2 != 0) v = kStepOneSite;
+  return v;
+}
+
+// Reads and clears the device status word (after a synchronisation).
+int check_status(flbm_ctx *c) {
+  int h = 0;
+  FLBM_CUDA(cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    FLBM_CUDA(cudaMemset(c->d_status, 0, sizeof(int)));
+    return fail(FLBM_ETIMEOUT, "a bounded wait in the pipelined step kernel gave up; the state is not valid");
+  }
   return FLBM_OK;
 }
 
@@ -279,12 +319,18 @@ int flbm_create_ex(flbm_ctx **out, int lattice, const int64_t dims[3], const dou
   const size_t acc_bytes = sizeof(double) * stats_record_len(c->Q);
   e = cudaMalloc(&c->d_acc, acc_bytes);
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_acc, acc_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     release(c);
     return fail(FLBM_ENOMEM, "cannot allocate statistics buffers");
   }
   fill_args(c);
+  if (const char *env = std::getenv("FLBM_STEP_VARIANT")) {
+    const int v = std::atoi(env);
+    if (v >= kStepAuto && v <= kStepVariantMax) c->variant = v;
+  }
   // Rest state f = w rho0: every stored deviation is zero (also for BF16/FP16 bits).
   e = cudaMemsetAsync(c->f, 0, need, c->stream);
   if (e != cudaSuccess) {
@@ -328,7 +374,8 @@ int flbm_step(flbm_ctx *c, int64_t n) {
   for (int64_t s = 0; s < n; ++s) {
     c->args.step_lo = uint32_t(uint64_t(c->step));
     c->args.step_hi = uint32_t(uint64_t(c->step) >> 32);
-    FLBM_CUDA(launch_step(c->D, c->storage, int(c->step & 1), noise, c->args, c->stream));
+    FLBM_CUDA(launch_step(c->D, c->storage, resolve_variant(c), int(c->step & 1), noise, c->shear,
+                          c->args, c->stream));
     ++c->step;
   }
   return FLBM_OK;
@@ -345,6 +392,8 @@ int flbm_stats(flbm_ctx *c, flbm_stats_t *out) {
   FLBM_CUDA(cudaMemcpyAsync(c->h_acc, c->d_acc, sizeof(double) * stats_record_len(c->Q),
                             cudaMemcpyDeviceToHost, c->stream));
   FLBM_CUDA(cudaStreamSynchronize(c->stream));
+  const int status = check_status(c);
+  if (status != FLBM_OK) return status;
   fill_stats(c, c->h_acc, c->step, out);
   if (out->nonfinite > 0)
     return fail(FLBM_ENUMERIC, "%lld sites hold non-finite values at step %lld",
@@ -534,11 +583,107 @@ int flbm_load(flbm_ctx *c, const void *host, size_t bytes) {
   return FLBM_OK;
 }
 
+int flbm_set_step_variant(flbm_ctx *c, int variant) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (variant < kStepAuto || variant > kStepVariantMax)
+    return fail(FLBM_EINVAL, "variant %d is not one of 0..%d", variant, int(kStepVariantMax));
+  c->variant = variant;
+  return FLBM_OK;
+}
+
+int flbm_get_step_variant(const flbm_ctx *c) { return c ? resolve_variant(c) : -1; }
+
+int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (trial_steps < 2) return fail(FLBM_EINVAL, "trial_steps must be >= 2");
+  DeviceGuard g(c->device);
+  // Cache: one choice per (device, lattice, storage, nx parity, size class, noise).
+  cudaDeviceProp prop;
+  FLBM_CUDA(cudaGetDeviceProperties(&prop, c->device));
+  int size_class = 0;
+  for (long long n = c->N; n > 1; n >>= 1) ++size_class;
+  char key[320];
+  std::snprintf(key, sizeof(key), "%s|%d|%d|%d|%d|%d|%d", prop.name, c->lattice, c->storage,
+                int(c->dims[0] % 2), size_class, c->kBT > 0.0 ? 1 : 0, c->shear ? 1 : 0);
+  static std::mutex mu;
+  static std::map<std::string, int> cache;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      c->variant = it->second;
+      if (chosen) *chosen = it->second;
+      return FLBM_OK;
+    }
+  }
+  // Trial steps run on a copy of the state, which is restored afterwards; the step
+  // counter is left unchanged, so tuning does not alter the simulation.
+  void *backup = nullptr;
+  if (cudaMalloc(&backup, c->f_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FLBM_ENOMEM, "cannot allocate %zu bytes for the autotuner's state copy", c->f_bytes);
+  }
+  int st = FLBM_OK;
+  float best = 1e30f;
+  int best_v = resolve_variant(c);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int64_t step0 = c->step;
+  const int saved_variant = c->variant;
+  do {
+    if (cudaMemcpyAsync(backup, c->f, c->f_bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      st = fail(FLBM_ECUDA, "autotune set-up: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    const int candidates[4] = {kStepOneSite, kStepPair, kStepPairRolled, kStepPipelined};
+    for (int v : candidates) {
+      if (v != kStepOneSite && c->dims[0] % 2 != 0) continue;
+      if (v == kStepPipelined && !pipe_applicable(c->D, c->storage, int(c->dims[0]))) continue;
+      c->variant = v;
+      if ((st = flbm_step(c, 2)) != FLBM_OK) break;  // warm-up (both parities)
+      cudaEventRecord(e0, c->stream);
+      if ((st = flbm_step(c, trial_steps)) != FLBM_OK) break;
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        st = fail(FLBM_ECUDA, "autotune timing failed");
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_v = v;
+      }
+      c->step = step0;
+      if (cudaMemcpyAsync(c->f, backup, c->f_bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+        st = fail(FLBM_ECUDA, "autotune restore failed");
+        break;
+      }
+    }
+  } while (false);
+  cudaStreamSynchronize(c->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(backup);
+  c->step = step0;
+  if (st != FLBM_OK) {
+    c->variant = saved_variant;
+    return st;
+  }
+  c->variant = best_v;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best_v;
+  }
+  if (chosen) *chosen = best_v;
+  return FLBM_OK;
+}
+
 int flbm_sync(flbm_ctx *c) {
   if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
   DeviceGuard g(c->device);
   FLBM_CUDA(cudaStreamSynchronize(c->stream));
-  return FLBM_OK;
+  return check_status(c);
 }
 
 const char *flbm_last_error(void) { return g_last_error.c_str(); }

@@ -20,6 +20,7 @@
 #include <cuda_fp16.h>
 
 #include "lattice.cuh"
+#include "vec.cuh"
 
 namespace flbm {
 
@@ -42,45 +43,49 @@ struct Storage<__half> {
   __device__ __forceinline__ static void store(__half *p, float v) { *p = __float2half_rn(v); }
 };
 
-// ---- 1-D building blocks ---------------------------------------------------------
+// ---- 1-D building blocks (T = float: one site; T = float2: two sites) -----------------
 // In: p0 = v(c=-1), p1 = v(c=0), p2 = v(c=+1). Out: p0 = sum v, p1 = sum c v,
 // p2 = sum (c^2 - cs^2) v.
-__device__ __forceinline__ void raw_fwd(float &p0, float &p1, float &p2) {
-  const float e = p2 + p0;
-  const float s = p1 + e;
-  const float d = p2 - p0;
-  p2 = fmaf(-kCs2, s, e);
+template <typename T>
+__device__ __forceinline__ void raw_fwd(T &p0, T &p1, T &p2) {
+  const T e = vadd(p2, p0);
+  const T s = vadd(p1, e);
+  const T d = vsub(p2, p0);
+  p2 = vfma(splat<T>(-kCs2), s, e);
   p1 = d;
   p0 = s;
 }
 
 // Inverse of raw_fwd.
-__device__ __forceinline__ void raw_inv(float &p0, float &p1, float &p2) {
-  const float s = p0, d = p1;
-  const float e = fmaf(kCs2, s, p2);
-  p1 = s - e;
-  p2 = 0.5f * (e + d);
-  p0 = 0.5f * (e - d);
+template <typename T>
+__device__ __forceinline__ void raw_inv(T &p0, T &p1, T &p2) {
+  const T s = p0, d = p1;
+  const T e = vfma(splat<T>(kCs2), s, p2);
+  p1 = vsub(s, e);
+  p2 = vmul(splat<T>(0.5f), vadd(e, d));
+  p0 = vmul(splat<T>(0.5f), vsub(e, d));
 }
 
-// Raw -> central moments along one axis with velocity component u.
-__device__ __forceinline__ void shift_fwd(float &m0, float &m1, float &m2, float u) {
-  const float k1 = fmaf(-u, m0, m1);
-  m2 = fmaf(-u, m1 + k1, m2);
+// Raw -> central moments along one axis; nu = -u (velocity component, negated).
+template <typename T>
+__device__ __forceinline__ void shift_fwd(T &m0, T &m1, T &m2, T nu) {
+  const T k1 = vfma(nu, m0, m1);
+  m2 = vfma(nu, vadd(m1, k1), m2);
   m1 = k1;
 }
 
-// Central -> raw moments along one axis (inverse of shift_fwd).
-__device__ __forceinline__ void shift_inv(float &k0, float &k1, float &k2, float u) {
-  const float r1 = fmaf(u, k0, k1);
-  k2 = fmaf(u, k1 + r1, k2);
+// Central -> raw moments along one axis (inverse of shift_fwd), velocity component u.
+template <typename T>
+__device__ __forceinline__ void shift_inv(T &k0, T &k1, T &k2, T u) {
+  const T r1 = vfma(u, k0, k1);
+  k2 = vfma(u, vadd(k1, r1), k2);
   k1 = r1;
 }
 
 // ---- tile transforms ---------------------------------------------------------------
 // Tile layout: F[z][y][x]; for D = 2 only the plane z = 1 is used.
-template <int D>
-__device__ __forceinline__ void tile_raw_fwd(float (&F)[3][3][3]) {
+template <int D, typename T>
+__device__ __forceinline__ void tile_raw_fwd(T (&F)[3][3][3]) {
   constexpr int z0 = (D == 3) ? 0 : 1, z1 = (D == 3) ? 3 : 2;
 #pragma unroll
   for (int z = z0; z < z1; ++z)
@@ -98,8 +103,8 @@ __device__ __forceinline__ void tile_raw_fwd(float (&F)[3][3][3]) {
   }
 }
 
-template <int D>
-__device__ __forceinline__ void tile_raw_inv(float (&F)[3][3][3]) {
+template <int D, typename T>
+__device__ __forceinline__ void tile_raw_inv(T (&F)[3][3][3]) {
   constexpr int z0 = (D == 3) ? 0 : 1, z1 = (D == 3) ? 3 : 2;
   if (D == 3) {
 #pragma unroll
@@ -117,27 +122,28 @@ __device__ __forceinline__ void tile_raw_inv(float (&F)[3][3][3]) {
     for (int y = 0; y < 3; ++y) raw_inv(F[z][y][0], F[z][y][1], F[z][y][2]);
 }
 
-template <int D>
-__device__ __forceinline__ void tile_shift_fwd(float (&F)[3][3][3], float ux, float uy, float uz) {
+// Central shift of all moments with the negated velocity (nux, nuy, nuz).
+template <int D, typename T>
+__device__ __forceinline__ void tile_shift_fwd(T (&F)[3][3][3], T nux, T nuy, T nuz) {
   constexpr int z0 = (D == 3) ? 0 : 1, z1 = (D == 3) ? 3 : 2;
 #pragma unroll
   for (int z = z0; z < z1; ++z)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) shift_fwd(F[z][b][0], F[z][b][1], F[z][b][2], ux);
+    for (int b = 0; b < 3; ++b) shift_fwd(F[z][b][0], F[z][b][1], F[z][b][2], nux);
 #pragma unroll
   for (int z = z0; z < z1; ++z)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) shift_fwd(F[z][0][a], F[z][1][a], F[z][2][a], uy);
+    for (int a = 0; a < 3; ++a) shift_fwd(F[z][0][a], F[z][1][a], F[z][2][a], nuy);
   if (D == 3) {
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) shift_fwd(F[0][b][a], F[1][b][a], F[2][b][a], uz);
+      for (int a = 0; a < 3; ++a) shift_fwd(F[0][b][a], F[1][b][a], F[2][b][a], nuz);
   }
 }
 
-template <int D>
-__device__ __forceinline__ void tile_shift_inv(float (&F)[3][3][3], float ux, float uy, float uz) {
+template <int D, typename T>
+__device__ __forceinline__ void tile_shift_inv(T (&F)[3][3][3], T ux, T uy, T uz) {
   constexpr int z0 = (D == 3) ? 0 : 1, z1 = (D == 3) ? 3 : 2;
   if (D == 3) {
 #pragma unroll
@@ -156,8 +162,8 @@ __device__ __forceinline__ void tile_shift_inv(float (&F)[3][3][3], float ux, fl
 }
 
 // Moment (a, b, c) of the tile after the forward transforms (c = 0 for D = 2).
-template <int D>
-__device__ __forceinline__ float &mom(float (&F)[3][3][3], int a, int b, int c) {
+template <int D, typename T>
+__device__ __forceinline__ T &mom(T (&F)[3][3][3], int a, int b, int c) {
   return D == 3 ? F[c][b][a] : F[1][b][a];
 }
 
@@ -248,20 +254,147 @@ __device__ __forceinline__ void store_streamed(S *__restrict__ f, long long plan
       }
 }
 
-// Forward part shared by the step and the statistics: raw moments of the deviation
-// tile, rho and u (Eq. macro), then central moments with entry (0,0,0) = rho.
-template <int D>
-__device__ __forceinline__ void site_central_moments(float (&F)[3][3][3], float rho0, float &drho,
-                                                     float &rho, float &ux, float &uy, float &uz) {
+// ---- two sites per thread: x0 and x0 + 1 (x0 even, nx even) ------------------------------
+// Pair loads/stores of two consecutive x; the array is 2-element aligned because nx is
+// even and the buffer is 256-byte aligned.
+template <typename S>
+struct Storage2;
+template <>
+struct Storage2<float> {
+  __device__ __forceinline__ static float2 load(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+  __device__ __forceinline__ static void store(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+};
+template <>
+struct Storage2<__nv_bfloat16> {
+  __device__ __forceinline__ static float2 load(const __nv_bfloat16 *p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+  }
+  __device__ __forceinline__ static void store(__nv_bfloat16 *p, float2 v) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
+  }
+};
+template <>
+struct Storage2<__half> {
+  __device__ __forceinline__ static float2 load(const __half *p) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+  }
+  __device__ __forceinline__ static void store(__half *p, float2 v) {
+    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.x, v.y);
+  }
+};
+
+// Site indices of a thread's pair and the periodic row / plane offsets of its block.
+// y and z are fixed per block, so dy and dz are the same for every thread of it; only
+// s0, sm1 and sp2 (the x seam) vary between threads.
+struct Addr2 {
+  long long s0;          // site x0
+  long long sm1, sp2;    // sites x0 - 1 and x0 + 2 of the same row (periodic)
+  long long dy[3];       // offset of row y - 1, y, y + 1 (periodic)
+  long long dz[3];       // offset of plane z - 1, z, z + 1 (periodic)
+};
+
+__device__ __forceinline__ Addr2 addr2(int x0, int y, int z, int nx, int ny, int nz) {
+  Addr2 a;
+  a.s0 = ((long long)z * ny + y) * nx + x0;
+  a.sm1 = a.s0 + (x0 == 0 ? nx - 1 : -1);
+  a.sp2 = a.s0 + (x0 + 2 == nx ? 2 - nx : 2);
+  const long long row = nx, pl = (long long)nx * ny;
+  a.dy[0] = (y == 0) ? (long long)(ny - 1) * row : -row;
+  a.dy[1] = 0;
+  a.dy[2] = (y == ny - 1) ? -(long long)(ny - 1) * row : row;
+  a.dz[0] = (z == 0) ? (long long)(nz - 1) * pl : -pl;
+  a.dz[1] = 0;
+  a.dz[2] = (z == nz - 1) ? -(long long)(nz - 1) * pl : pl;
+  return a;
+}
+
+// As load_logical, for the pair: lane x holds site x0, lane y site x0 + 1.
+template <int D, typename S, int PARITY>
+__device__ __forceinline__ void load_logical2(const S *__restrict__ f, long long plane, const Addr2 &ad,
+                                              float2 (&F)[3][3][3]) {
+  constexpr int z0 = (D == 3) ? -1 : 0, z1 = (D == 3) ? 1 : 0;
+#pragma unroll
+  for (int dz = z0; dz <= z1; ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = Lat<D>::index(dx, dy, dz);
+        float2 v;
+        if (PARITY == 0) {
+          v = Storage2<S>::load(f + i * plane + ad.s0);
+        } else {
+          // f_i(x) = A[opposite(i)][x - c_i]
+          const S *b = f + opposite<D>(i) * plane + ad.dy[1 - dy] + ad.dz[1 - dz];
+          if (dx == 0) {
+            v = Storage2<S>::load(b + ad.s0);
+          } else if (dx == 1) {
+            v.x = Storage<S>::load(b + ad.sm1);
+            v.y = Storage<S>::load(b + ad.s0);
+          } else {
+            v.x = Storage<S>::load(b + ad.s0 + 1);
+            v.y = Storage<S>::load(b + ad.sp2);
+          }
+        }
+        F[dz + 1][dy + 1][dx + 1] = v;
+      }
+}
+
+// As store_streamed, for the pair.
+template <int D, typename S, int PARITY>
+__device__ __forceinline__ void store_streamed2(S *__restrict__ f, long long plane, const Addr2 &ad,
+                                                const float2 (&F)[3][3][3]) {
+  constexpr int z0 = (D == 3) ? -1 : 0, z1 = (D == 3) ? 1 : 0;
+#pragma unroll
+  for (int dz = z0; dz <= z1; ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = Lat<D>::index(dx, dy, dz);
+        const float2 v = F[dz + 1][dy + 1][dx + 1];
+        if (PARITY == 0) {
+          Storage2<S>::store(f + opposite<D>(i) * plane + ad.s0, v);
+        } else {
+          // f*_i(x) goes to A[i][x + c_i]
+          S *b = f + i * plane + ad.dy[1 + dy] + ad.dz[1 + dz];
+          if (dx == 0) {
+            Storage2<S>::store(b + ad.s0, v);
+          } else if (dx == 1) {
+            Storage<S>::store(b + ad.s0 + 1, v.x);
+            Storage<S>::store(b + ad.sp2, v.y);
+          } else {
+            Storage<S>::store(b + ad.sm1, v.x);
+            Storage<S>::store(b + ad.s0, v.y);
+          }
+        }
+      }
+}
+
+// Raw moments of the deviation tile and rho, u (Eq. macro); entry (0,0,0) stays rho - rho0.
+template <int D, typename T>
+__device__ __forceinline__ void site_macros(T (&F)[3][3][3], float rho0, T &drho, T &rho, T &ux, T &uy,
+                                            T &uz) {
   tile_raw_fwd<D>(F);
   drho = mom<D>(F, 0, 0, 0);
-  rho = rho0 + drho;
-  const float inv_rho = 1.0f / rho;
-  ux = mom<D>(F, 1, 0, 0) * inv_rho;
-  uy = mom<D>(F, 0, 1, 0) * inv_rho;
-  uz = (D == 3) ? mom<D>(F, 0, 0, 1) * inv_rho : 0.0f;
+  rho = vadd(splat<T>(rho0), drho);
+  T inv_rho;
+#pragma unroll
+  for (int l = 0; l < Lanes<T>::n; ++l) set_lane(inv_rho, l, 1.0f / lane(rho, l));
+  ux = vmul(mom<D>(F, 1, 0, 0), inv_rho);
+  uy = vmul(mom<D>(F, 0, 1, 0), inv_rho);
+  uz = (D == 3) ? vmul(mom<D>(F, 0, 0, 1), inv_rho) : splat<T>(0.0f);
+}
+
+// Forward part shared by the step and the statistics: raw moments of the deviation
+// tile, rho and u (Eq. macro), then central moments with entry (0,0,0) = rho.
+template <int D, typename T>
+__device__ __forceinline__ void site_central_moments(T (&F)[3][3][3], float rho0, T &drho, T &rho,
+                                                     T &ux, T &uy, T &uz) {
+  site_macros<D>(F, rho0, drho, rho, ux, uy, uz);
   mom<D>(F, 0, 0, 0) = rho;
-  tile_shift_fwd<D>(F, ux, uy, uz);
+  const T m1 = splat<T>(-1.0f);
+  tile_shift_fwd<D>(F, vmul(m1, ux), vmul(m1, uy), vmul(m1, uz));
 }
 
 }  // namespace flbm

@@ -1,4 +1,5 @@
-// The stochastic central-moment collision of one site, on the register tile.
+// The stochastic central-moment collision of one site (T = float) or of two sites at
+// once (T = float2), on the register tile.
 //
 //   k*_v = (1 - L_v) k_v + L_v k^eq_v + I~_v phi_v eta_v        (Eq. cm_collision)
 //   k^eq = (rho, 0, ..., 0)                                     (Sec. II-B, Sec. II-C)
@@ -16,66 +17,140 @@
 
 namespace flbm {
 
-template <int D, bool NOISE>
-__device__ __forceinline__ void collide_tile(float (&F)[3][3][3], float rho0, const float *om,
-                                             const float *phc, uint32_t site, uint32_t step_lo,
-                                             uint32_t step_hi, uint32_t key0, uint32_t key1) {
-  float drho, rho, ux, uy, uz;
-  site_central_moments<D>(F, rho0, drho, rho, ux, uy, uz);
-  const float srho = sqrtf(rho);
-  if (D == 3) {
+// D3Q27: adds phi_v eta_v (eta already scaled by sqrt(rho)) to the four modes that
+// Philox block BLK feeds, v = 4 + 4 BLK + j (j < 4, v < 27).
+template <int BLK, typename T>
+__device__ __forceinline__ void add_noise_block(T (&F)[3][3][3], const float *phc, const T (&z)[4]) {
 #pragma unroll
-    for (int v = 4; v < 27; ++v) {
+  for (int j = 0; j < 4; ++j) {
+    const int v = 4 + 4 * BLK + j;
+    if (v < 27) {
       const int t = d3q27_mode_tensor(v);
-      float &k = F[t / 9][(t / 3) % 3][t % 3];
-      k = om[v] * k;
+      T &k = F[t / 9][(t / 3) % 3][t % 3];
+      k = vfma(splat<T>(phc[v]), z[j], k);
     }
-    if (NOISE) {
+  }
+}
+
+// ROLLED: generate the D3Q27 noise in a loop over the six Philox blocks instead of six
+// unrolled copies, which shrinks the kernel's instruction footprint about fourfold (the
+// unrolled body overflows the instruction cache); the arithmetic is identical.
+// SHEAR: the caller guarantees the paper's relaxation structure, L_v = 1 for every
+// non-conserved mode except the shear modes (D3Q27 v = 7, 8, 9; D2Q9 v = 4, 5; Sec. II-C
+// and II-B). Then k*_v = phi_v eta_v needs no pre-collision value, and only the shear
+// central moments are formed, directly as k_ab = r_ab - rho u_a u_b (Sec. II-C prints
+// k7-k9 in this form) instead of through the full velocity shift.
+template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false>
+__device__ __forceinline__ void collide_tile(T (&F)[3][3][3], float rho0, const float *om,
+                                             const float *phc, uint32_t site0, uint32_t step_lo,
+                                             uint32_t step_hi, const uint32_t *ks0,
+                                             const uint32_t *ks1) {
+  T drho, rho, ux, uy, uz;
+  if (SHEAR) {
+    site_macros<D>(F, rho0, drho, rho, ux, uy, uz);
+    mom<D>(F, 0, 0, 0) = rho;  // k*_0 = rho for the way back
+  } else {
+    site_central_moments<D>(F, rho0, drho, rho, ux, uy, uz);
+  }
+  T srho;
+#pragma unroll
+  for (int l = 0; l < Lanes<T>::n; ++l) set_lane(srho, l, sqrtf(lane(rho, l)));
+  if (D == 3) {
+    if (SHEAR) {
+      // raw (1,1,0), (1,0,1), (0,1,1) -> central; every other non-conserved mode restarts
+      // from k^eq = 0.
+      const T nrho = vmul(splat<T>(-1.0f), rho);
+      const T kxy = vfma(vmul(nrho, ux), uy, F[0][1][1]);
+      const T kxz = vfma(vmul(nrho, ux), uz, F[1][0][1]);
+      const T kyz = vfma(vmul(nrho, uy), uz, F[1][1][0]);
+#pragma unroll
+      for (int v = 4; v < 27; ++v) {
+        const int t = d3q27_mode_tensor(v);
+        F[t / 9][(t / 3) % 3][t % 3] = splat<T>(0.0f);
+      }
+      F[0][1][1] = vmul(splat<T>(om[7]), kxy);
+      F[1][0][1] = vmul(splat<T>(om[8]), kxz);
+      F[1][1][0] = vmul(splat<T>(om[9]), kyz);
+    } else {
+#pragma unroll
+      for (int v = 4; v < 27; ++v) {
+        const int t = d3q27_mode_tensor(v);
+        T &k = F[t / 9][(t / 3) % 3][t % 3];
+        k = vmul(splat<T>(om[v]), k);
+      }
+    }
+    if (NOISE && ROLLED) {
+#pragma unroll 1
+      for (int blk = 0; blk < 6; ++blk) {
+        T z[4];
+        normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, ks0, ks1, srho, z);
+        switch (blk) {  // block-uniform branch: modes 4 + 4 blk .. 7 + 4 blk
+          case 0: add_noise_block<0>(F, phc, z); break;
+          case 1: add_noise_block<1>(F, phc, z); break;
+          case 2: add_noise_block<2>(F, phc, z); break;
+          case 3: add_noise_block<3>(F, phc, z); break;
+          case 4: add_noise_block<4>(F, phc, z); break;
+          default: add_noise_block<5>(F, phc, z); break;
+        }
+      }
+    } else if (NOISE) {
 #pragma unroll
       for (int blk = 0; blk < 6; ++blk) {
-        const Normals4 n = normals4(site, step_lo, step_hi, (uint32_t)blk, key0, key1);
-        const float zz[4] = {n.z0, n.z1, n.z2, n.z3};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int v = 4 + 4 * blk + j;
-          if (v < 27) {
-            const int t = d3q27_mode_tensor(v);
-            float &k = F[t / 9][(t / 3) % 3][t % 3];
-            k = fmaf(srho * phc[v], zz[j], k);
-          }
+        T z[4];
+        normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, ks0, ks1, srho, z);
+        switch (blk) {
+          case 0: add_noise_block<0>(F, phc, z); break;
+          case 1: add_noise_block<1>(F, phc, z); break;
+          case 2: add_noise_block<2>(F, phc, z); break;
+          case 3: add_noise_block<3>(F, phc, z); break;
+          case 4: add_noise_block<4>(F, phc, z); break;
+          default: add_noise_block<5>(F, phc, z); break;
         }
       }
     }
-    F[0][0][1] = 0.0f;  // k*_1 (x momentum, central)
-    F[0][1][0] = 0.0f;  // k*_2
-    F[1][0][0] = 0.0f;  // k*_3
+    F[0][0][1] = splat<T>(0.0f);  // k*_1 (x momentum, central)
+    F[0][1][0] = splat<T>(0.0f);  // k*_2
+    F[1][0][0] = splat<T>(0.0f);  // k*_3
   } else {
     // D2Q9: modes 3 and 4 are the sum and difference of the (2,0) and (0,2) moments.
-    const float kxx = F[1][0][2], kyy = F[1][2][0];
-    float k3 = om[3] * (kxx + kyy);
-    float k4 = om[4] * (kxx - kyy);
-    float k5 = om[5] * F[1][1][1];
-    float k6 = om[6] * F[1][1][2];
-    float k7 = om[7] * F[1][2][1];
-    float k8 = om[8] * F[1][2][2];
-    if (NOISE) {
-      const Normals4 n0 = normals4(site, step_lo, step_hi, 0u, key0, key1);
-      const Normals4 n1 = normals4(site, step_lo, step_hi, 1u, key0, key1);
-      k3 = fmaf(srho * phc[3], n0.z0, k3);
-      k4 = fmaf(srho * phc[4], n0.z1, k4);
-      k5 = fmaf(srho * phc[5], n0.z2, k5);
-      k6 = fmaf(srho * phc[6], n0.z3, k6);
-      k7 = fmaf(srho * phc[7], n1.z0, k7);
-      k8 = fmaf(srho * phc[8], n1.z1, k8);
+    T k3, k4, k5, k6, k7, k8;
+    if (SHEAR) {
+      // k4 = r_xx - r_yy - rho (ux^2 - uy^2), k5 = r_xy - rho ux uy (Sec. II-B); the
+      // other non-conserved modes restart from k^eq = 0.
+      const T nrho = vmul(splat<T>(-1.0f), rho);
+      const T d2 = vsub(vmul(ux, ux), vmul(uy, uy));
+      k4 = vmul(splat<T>(om[4]), vfma(nrho, d2, vsub(F[1][0][2], F[1][2][0])));
+      k5 = vmul(splat<T>(om[5]), vfma(vmul(nrho, ux), uy, F[1][1][1]));
+      k3 = k6 = k7 = k8 = splat<T>(0.0f);
+    } else {
+      const T kxx = F[1][0][2], kyy = F[1][2][0];
+      k3 = vmul(splat<T>(om[3]), vadd(kxx, kyy));
+      k4 = vmul(splat<T>(om[4]), vsub(kxx, kyy));
+      k5 = vmul(splat<T>(om[5]), F[1][1][1]);
+      k6 = vmul(splat<T>(om[6]), F[1][1][2]);
+      k7 = vmul(splat<T>(om[7]), F[1][2][1]);
+      k8 = vmul(splat<T>(om[8]), F[1][2][2]);
     }
-    F[1][0][2] = 0.5f * (k3 + k4);
-    F[1][2][0] = 0.5f * (k3 - k4);
+    if (NOISE) {
+      T z0[4], z1[4];
+      normals4_scaled<T>(site0, step_lo, step_hi, 0u, ks0, ks1, srho, z0);
+      normals4_scaled<T>(site0, step_lo, step_hi, 1u, ks0, ks1, srho, z1);
+      k3 = vfma(splat<T>(phc[3]), z0[0], k3);
+      k4 = vfma(splat<T>(phc[4]), z0[1], k4);
+      k5 = vfma(splat<T>(phc[5]), z0[2], k5);
+      k6 = vfma(splat<T>(phc[6]), z0[3], k6);
+      k7 = vfma(splat<T>(phc[7]), z1[0], k7);
+      k8 = vfma(splat<T>(phc[8]), z1[1], k8);
+    }
+    const T h = splat<T>(0.5f);
+    F[1][0][2] = vmul(h, vadd(k3, k4));
+    F[1][2][0] = vmul(h, vsub(k3, k4));
     F[1][1][1] = k5;
     F[1][1][2] = k6;
     F[1][2][1] = k7;
     F[1][2][2] = k8;
-    F[1][0][1] = 0.0f;  // k*_1
-    F[1][1][0] = 0.0f;  // k*_2
+    F[1][0][1] = splat<T>(0.0f);  // k*_1
+    F[1][1][0] = splat<T>(0.0f);  // k*_2
   }
   // r* = N^{-1} k* (entry (0,0,0) = k*_0 = rho), then d* = M^{-1} r* - w rho0.
   tile_shift_inv<D>(F, ux, uy, uz);

@@ -20,7 +20,9 @@ struct StepArgs {
   int nx, ny, nz;
   float rho0;
   uint32_t key0, key1;        // noise key (seed)
+  uint32_t ks0[10], ks1[10];  // Philox round keys: key0 + r 0x9E3779B9, key1 + r 0xBB67AE85
   uint32_t step_lo, step_hi;  // step number of this update
+  int *status;        // device word: nonzero after a bounded wait gave up (pipelined kernel)
   float om[27];       // 1 - Lambda_v (conserved modes: unused)
   float phc[27];      // sqrt(kBT Lambda_v (2 - Lambda_v) b_v / cs^2); phi_v = sqrt(rho) phc_v
 };
@@ -29,8 +31,24 @@ struct StepArgs {
 int stats_nacc(int Q);
 inline int stats_record_len(int Q) { return stats_nacc(Q) + 1; }  // + non-finite count
 
-cudaError_t launch_step(int D, int storage, int parity, bool noise, const StepArgs &a,
-                        cudaStream_t s);
+// Step-kernel variants (the autotuner's search space; all compute the same update):
+// one site per thread; two sites per thread (nx even) with the noise loop unrolled or
+// rolled; or the bulk-copy pipelined persistent kernel (step_pipe.cu; needs
+// pipe_applicable). `shear` selects the specialisation for the paper's rate structure
+// (rate 1 for every non-conserved mode but the shear ones).
+enum StepVariant {
+  kStepAuto = 0,
+  kStepOneSite = 1,
+  kStepPair = 2,
+  kStepPairRolled = 3,
+  kStepPipelined = 4,
+  kStepVariantMax = 4
+};
+bool pipe_applicable(int D, int storage, int nx);
+cudaError_t launch_step(int D, int storage, int variant, int parity, bool noise, bool shear,
+                        const StepArgs &a, cudaStream_t s);
+cudaError_t launch_step_pipelined(int D, int storage, int parity, bool noise, bool shear,
+                                  const StepArgs &a, cudaStream_t s);
 cudaError_t launch_stats(int D, int storage, int parity, const void *f, long long plane, int nx,
                          int ny, int nz, float rho0, double *acc, cudaStream_t s);
 cudaError_t launch_init(int D, int storage, void *f, long long plane, int nx, int ny, int nz,

@@ -12,6 +12,8 @@
 
 #include <cstdint>
 
+#include "vec.cuh"
+
 namespace flbm {
 
 struct Normals4 {
@@ -55,6 +57,133 @@ __device__ __forceinline__ Normals4 normals4(uint32_t site, uint32_t step_lo, ui
   box_muller(w.x, w.y, n.z0, n.z1);
   box_muller(w.z, w.w, n.z2, n.z3);
   return n;
+}
+
+// Philox4x32-10 with the round keys precomputed (k0[r] = key0 + r W0, k1[r] = key1 +
+// r W1); the 64-bit products give each round's high and low words in one multiply.
+__device__ __forceinline__ uint4 philox4x32_10_ks(uint4 ctr, const uint32_t *k0, const uint32_t *k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * ctr.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * ctr.z;
+    ctr = make_uint4((uint32_t)(p1 >> 32) ^ ctr.y ^ k0[round], (uint32_t)p1,
+                     (uint32_t)(p0 >> 32) ^ ctr.w ^ k1[round], (uint32_t)p0);
+  }
+  return ctr;
+}
+
+// Box-Muller with the angle reduced exactly in integers. For u_b = (m + 1/2) 2^-23,
+// m = w_b >> 9, the nearest half turn is h = round(2 u_b) (0, 1 or 2, from the top two
+// bits of w_b) and 2 pi u_b - h pi = (m - h 2^22 + 1/2) pi 2^-22, a number in
+// [-pi/2, pi/2] formed with one rounding. sin and cos of it are their Taylor series
+// (to r^13 and r^14; truncation below 7e-10), and cos(2 pi u_b) = (-1)^h cos r,
+// sin(2 pi u_b) = (-1)^h sin r. Checked against the FP64 definition over all 2^23 angle
+// codes: |error| < 2e-7.
+//
+// The radius: u_a = (2 m_a + 1) 2^-24 with y = 2 m_a + 1 an odd integer below 2^24, so
+// -2 ln u_a = -2 (ln y - 24 ln 2). y converts to FP32 exactly; the argument reduction
+// of Cody & Waite (Software Manual for the Elementary Functions, 1980) writes y = 2^k x
+// with x in [sqrt(1/2), sqrt(2)), and ln x = 2 atanh(s) = 2 (s + s^3/3 + ... + s^9/9),
+// s = (x - 1)/(x + 1), |s| < 0.172 (truncation below 1e-9 relative). x - 1 is exact,
+// so the result keeps its relative accuracy as u_a -> 1, where r -> 0. Checked against
+// the FP64 definition over all 2^23 codes: relative error of -2 ln u_a below 3e-7.
+constexpr float kAngleScale = 0x1p-22f * 3.14159265358979323846f;
+constexpr float kAngleOffset = 0x1p-23f * 3.14159265358979323846f;
+
+
+template <typename T>
+__device__ __forceinline__ void sincos_taylor(T r, T &s, T &c) {
+  const T r2 = vmul(r, r);
+  T p = vfma(r2, splat<T>(1.0f / 6227020800.0f), splat<T>(-1.0f / 39916800.0f));
+  p = vfma(p, r2, splat<T>(1.0f / 362880.0f));
+  p = vfma(p, r2, splat<T>(-1.0f / 5040.0f));
+  p = vfma(p, r2, splat<T>(1.0f / 120.0f));
+  p = vfma(p, r2, splat<T>(-1.0f / 6.0f));
+  s = vfma(vmul(r2, r), p, r);
+  T q = vfma(r2, splat<T>(-1.0f / 87178291200.0f), splat<T>(1.0f / 479001600.0f));
+  q = vfma(q, r2, splat<T>(-1.0f / 3628800.0f));
+  q = vfma(q, r2, splat<T>(1.0f / 40320.0f));
+  q = vfma(q, r2, splat<T>(-1.0f / 720.0f));
+  q = vfma(q, r2, splat<T>(1.0f / 24.0f));
+  q = vfma(q, r2, splat<T>(-0.5f));
+  c = vfma(q, r2, splat<T>(1.0f));
+}
+
+// (cos, sin) of h pi + r from (cos r, sin r), times rad.
+__device__ __forceinline__ void bm_finish(float s, float c, uint32_t half, float rad, float &za,
+                                          float &zb) {
+  const float rr = __int_as_float(__float_as_int(rad) ^ ((half & 1u) << 31));  // (-1)^h rad
+  za = rr * c;
+  zb = rr * s;
+}
+
+// Four normals of Philox block `blk` for each lane's site (lane l: site0 + l), each
+// multiplied by `scale` of its lane (the caller's sqrt(rho)).
+template <typename T>
+__device__ __forceinline__ void normals4_scaled(uint32_t site0, uint32_t step_lo, uint32_t step_hi,
+                                                uint32_t blk, const uint32_t *k0, const uint32_t *k1,
+                                                T scale, T (&z)[4]) {
+  constexpr int L = Lanes<T>::n;
+  float rad[L][2], ang_l[L][2];
+  uint32_t hturn[L][2];
+  uint32_t wav[L][2];
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    const uint4 w = philox4x32_10_ks(make_uint4(site0 + l, step_lo, step_hi, blk), k0, k1);
+    wav[l][0] = w.x;
+    wav[l][1] = w.z;
+    hturn[l][0] = (w.y >> 31) + ((w.y >> 30) & 1u);
+    ang_l[l][0] = fmaf((float)((int)(w.y >> 9) - (int)(hturn[l][0] << 22)), kAngleScale, kAngleOffset);
+    hturn[l][1] = (w.w >> 31) + ((w.w >> 30) & 1u);
+    ang_l[l][1] = fmaf((float)((int)(w.w >> 9) - (int)(hturn[l][1] << 22)), kAngleScale, kAngleOffset);
+  }
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    T x, kf;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      const uint32_t y = (wav[l][p] >> 8) | 1u;
+      const uint32_t ix = __float_as_uint((float)y) - 0x3F3504F3u;
+      set_lane(x, l, __uint_as_float((ix & 0x007FFFFFu) + 0x3F3504F3u));
+      set_lane(kf, l, (float)(((int)ix >> 23) - 24));
+    }
+    const T t = vsub(x, splat<T>(1.0f));
+    const T d = vadd(x, splat<T>(1.0f));
+    T rd;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      float r_;
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r_) : "f"(lane(d, l)));
+      set_lane(rd, l, r_);
+    }
+    const T sx = vmul(t, rd);
+    const T s2 = vmul(sx, sx);
+    T P = vfma(s2, splat<T>(-4.0f / 9.0f), splat<T>(-4.0f / 7.0f));  // -2 * 2 * (1/(2j+1))
+    P = vfma(P, s2, splat<T>(-4.0f / 5.0f));
+    P = vfma(P, s2, splat<T>(-4.0f / 3.0f));
+    P = vfma(P, s2, splat<T>(-4.0f));
+    const T a = vfma(kf, splat<T>(-1.38629436f), vmul(sx, P));  // -2 ln u_a (kf = k - 24)
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      const float al = lane(a, l);
+      rad[l][p] = al * rsqrtf(al) * lane(scale, l);
+    }
+  }
+
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    T ang, s, c;
+#pragma unroll
+    for (int l = 0; l < L; ++l) set_lane(ang, l, ang_l[l][p]);
+    sincos_taylor(ang, s, c);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      float za, zb;
+      bm_finish(lane(s, l), lane(c, l), hturn[l][p], rad[l][p], za, zb);
+      set_lane(z[2 * p], l, za);
+      set_lane(z[2 * p + 1], l, zb);
+    }
+  }
 }
 
 }  // namespace flbm

@@ -137,8 +137,9 @@ template <int D, typename S>
 cudaError_t launch_typed(int parity, const void *f, long long plane, int nx, int ny, int nz,
                          float rho0, double *acc, cudaStream_t s) {
   int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   const long long tiles = (plane + kStatsBlock - 1) / kStatsBlock;
   const long long cap = (long long)(sms > 0 ? sms : 1) * 8;
   const int grid = (int)(tiles < cap ? tiles : cap);

@@ -15,11 +15,20 @@
 // reads, so no two threads race and no second lattice is needed. Logical populations:
 // even state f_i(x) = A[i][x]; odd state f_i(x) = A[opposite(i)][x - c_i].
 //
-// Layout: structure of arrays A[q][z][y][x], x fastest; one thread per site, blocks
-// of 128 consecutive x, grid (ceil(nx/128), ny, nz); warps touch 128-byte runs per
-// population (FP32), so every load and store is coalesced (odd steps are shifted by
-// one element, which costs no extra DRAM traffic).
+// Layout: structure of arrays A[q][z][y][x], x fastest. Kernels (launch variants, all
+// computing the same update; see StepVariant in internal.h):
+//   step_kernel  - one site per thread, blocks of 128 consecutive x, grid
+//                  (ceil(nx/128), ny, nz); any nx;
+//   step2_kernel - two sites per thread (x0 = 2 t, x0 + 1; nx even): every floating-
+//                  point step runs as packed FP32x2, population pairs move as one 8-byte
+//                  (FP32) or 4-byte (16-bit) access, per-population address offsets are
+//                  block-uniform; capped at 128 registers (4 blocks of 4 warps per SM);
+//                  the noise loop is unrolled or rolled (smaller code).
+// Warps touch contiguous runs of every population, so all accesses are coalesced (odd
+// steps are shifted by one element, which costs no extra DRAM traffic).
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "collide.cuh"
 #include "internal.h"
@@ -27,7 +36,7 @@
 namespace flbm {
 namespace {
 
-template <int D, typename S, int PARITY, bool NOISE>
+template <int D, typename S, int PARITY, bool NOISE, bool SHEAR>
 __global__ void __launch_bounds__(kStepBlock) step_kernel(const StepArgs a) {
   const int x = blockIdx.x * kStepBlock + threadIdx.x;
   if (x >= a.nx) return;
@@ -38,40 +47,77 @@ __global__ void __launch_bounds__(kStepBlock) step_kernel(const StepArgs a) {
   float F[3][3][3];
   load_logical<D, S, PARITY>(f, a.plane, nb, F);
   const uint32_t site = (uint32_t)(x + (long long)a.nx * (y + (long long)a.ny * z));
-  collide_tile<D, NOISE>(F, a.rho0, a.om, a.phc, site, a.step_lo, a.step_hi, a.key0, a.key1);
+  collide_tile<D, NOISE, float, false, SHEAR>(F, a.rho0, a.om, a.phc, site, a.step_lo, a.step_hi, a.ks0,
+                                              a.ks1);
   store_streamed<D, S, PARITY>(f, a.plane, nb, F);
 }
 
-template <int D, typename S>
-cudaError_t launch_typed(int parity, bool noise, const StepArgs &a, cudaStream_t s) {
-  const dim3 grid((a.nx + kStepBlock - 1) / kStepBlock, a.ny, a.nz);
+template <int D, typename S, int PARITY, bool NOISE, bool ROLLED, bool SHEAR>
+__global__ void __launch_bounds__(kStepBlock, 4) step2_kernel(const StepArgs a) {
+  const int x0 = 2 * (blockIdx.x * kStepBlock + threadIdx.x);
+  if (x0 >= a.nx) return;
+  const Addr2 ad = addr2(x0, blockIdx.y, blockIdx.z, a.nx, a.ny, a.nz);
+  S *__restrict__ f = static_cast<S *>(a.f);
+
+  float2 F[3][3][3];
+  load_logical2<D, S, PARITY>(f, a.plane, ad, F);
+  collide_tile<D, NOISE, float2, ROLLED, SHEAR>(F, a.rho0, a.om, a.phc, (uint32_t)ad.s0, a.step_lo,
+                                                a.step_hi, a.ks0, a.ks1);
+  store_streamed2<D, S, PARITY>(f, a.plane, ad, F);
+}
+
+template <typename S>
+constexpr int storage_code() {
+  return sizeof(S) == 4 ? 0 : (std::is_same<S, __nv_bfloat16>::value ? 1 : 2);
+}
+
+template <int D, typename S, int PARITY, bool NOISE, bool SHEAR>
+cudaError_t launch_kernel(int variant, const StepArgs &a, cudaStream_t s) {
   const dim3 block(kStepBlock);
-  if (parity == 0) {
-    if (noise)
-      step_kernel<D, S, 0, true><<<grid, block, 0, s>>>(a);
+  if (variant == kStepPair || variant == kStepPairRolled) {
+    const dim3 grid((a.nx / 2 + kStepBlock - 1) / kStepBlock, a.ny, a.nz);
+    if (variant == kStepPairRolled)
+      step2_kernel<D, S, PARITY, NOISE, true, SHEAR><<<grid, block, 0, s>>>(a);
     else
-      step_kernel<D, S, 0, false><<<grid, block, 0, s>>>(a);
+      step2_kernel<D, S, PARITY, NOISE, false, SHEAR><<<grid, block, 0, s>>>(a);
   } else {
-    if (noise)
-      step_kernel<D, S, 1, true><<<grid, block, 0, s>>>(a);
-    else
-      step_kernel<D, S, 1, false><<<grid, block, 0, s>>>(a);
+    const dim3 grid((a.nx + kStepBlock - 1) / kStepBlock, a.ny, a.nz);
+    step_kernel<D, S, PARITY, NOISE, SHEAR><<<grid, block, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
 
+template <int D, typename S>
+cudaError_t launch_typed(int variant, int parity, bool noise, bool shear, const StepArgs &a,
+                         cudaStream_t s) {
+  if (variant == kStepPipelined)
+    return launch_step_pipelined(D, storage_code<S>(), parity, noise, shear, a, s);
+  if (parity == 0) {
+    if (noise)
+      return shear ? launch_kernel<D, S, 0, true, true>(variant, a, s)
+                   : launch_kernel<D, S, 0, true, false>(variant, a, s);
+    return shear ? launch_kernel<D, S, 0, false, true>(variant, a, s)
+                 : launch_kernel<D, S, 0, false, false>(variant, a, s);
+  }
+  if (noise)
+    return shear ? launch_kernel<D, S, 1, true, true>(variant, a, s)
+                 : launch_kernel<D, S, 1, true, false>(variant, a, s);
+  return shear ? launch_kernel<D, S, 1, false, true>(variant, a, s)
+               : launch_kernel<D, S, 1, false, false>(variant, a, s);
+}
+
 }  // namespace
 
-cudaError_t launch_step(int D, int storage, int parity, bool noise, const StepArgs &a,
-                        cudaStream_t s) {
+cudaError_t launch_step(int D, int storage, int variant, int parity, bool noise, bool shear,
+                        const StepArgs &a, cudaStream_t s) {
   if (D == 3) {
-    if (storage == 0) return launch_typed<3, float>(parity, noise, a, s);
-    if (storage == 1) return launch_typed<3, __nv_bfloat16>(parity, noise, a, s);
-    return launch_typed<3, __half>(parity, noise, a, s);
+    if (storage == 0) return launch_typed<3, float>(variant, parity, noise, shear, a, s);
+    if (storage == 1) return launch_typed<3, __nv_bfloat16>(variant, parity, noise, shear, a, s);
+    return launch_typed<3, __half>(variant, parity, noise, shear, a, s);
   }
-  if (storage == 0) return launch_typed<2, float>(parity, noise, a, s);
-  if (storage == 1) return launch_typed<2, __nv_bfloat16>(parity, noise, a, s);
-  return launch_typed<2, __half>(parity, noise, a, s);
+  if (storage == 0) return launch_typed<2, float>(variant, parity, noise, shear, a, s);
+  if (storage == 1) return launch_typed<2, __nv_bfloat16>(variant, parity, noise, shear, a, s);
+  return launch_typed<2, __half>(variant, parity, noise, shear, a, s);
 }
 
 }  // namespace flbm

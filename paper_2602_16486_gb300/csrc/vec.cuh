@@ -1,0 +1,57 @@
+// Arithmetic on one site (float) or on two sites at once (float2). The float2 forms map
+// to Blackwell's packed FP32 instructions (__fadd2_rn / __fmul2_rn / __ffma2_rn): one
+// instruction performs the same IEEE round-to-nearest operation on both halves, so a
+// thread that owns two lattice sites issues each step of the per-site algebra once.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace flbm {
+
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+
+template <typename T>
+__device__ __forceinline__ T splat(float x);
+template <>
+__device__ __forceinline__ float splat<float>(float x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ float2 splat<float2>(float x) {
+  return make_float2(x, x);
+}
+
+// Number of sites a value of type T carries.
+template <typename T>
+struct Lanes;
+template <>
+struct Lanes<float> {
+  static constexpr int n = 1;
+};
+template <>
+struct Lanes<float2> {
+  static constexpr int n = 2;
+};
+
+// Per-lane access (lane 0 = first site, lane 1 = second site).
+__device__ __forceinline__ float lane(float v, int) { return v; }
+__device__ __forceinline__ float lane(float2 v, int l) { return l == 0 ? v.x : v.y; }
+__device__ __forceinline__ void set_lane(float &v, int, float x) { v = x; }
+__device__ __forceinline__ void set_lane(float2 &v, int l, float x) {
+  if (l == 0)
+    v.x = x;
+  else
+    v.y = x;
+}
+
+}  // namespace flbm

@@ -89,6 +89,9 @@ def _load():
         "flbm_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
         "flbm_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
         "flbm_sync": (ctypes.c_int, [vp]),
+        "flbm_set_step_variant": (ctypes.c_int, [vp, ctypes.c_int]),
+        "flbm_get_step_variant": (ctypes.c_int, [vp]),
+        "flbm_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "flbm_stats_noalloc": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_double, vp, vp, ctypes.POINTER(flbm_stats_t)]),
         "flbm_last_error": (ctypes.c_char_p, []),
@@ -262,6 +265,20 @@ def flbm_stats_noalloc(lattice, dims, storage, parity, rho0, dev_populations, cu
     return out.to_dict()
 
 
+def flbm_set_step_variant(ctx, variant):
+    _check(_lib.flbm_set_step_variant(ctx, int(variant)))
+
+
+def flbm_get_step_variant(ctx):
+    return int(_lib.flbm_get_step_variant(ctx))
+
+
+def flbm_autotune(ctx, trial_steps=10):
+    chosen = ctypes.c_int(-1)
+    _check(_lib.flbm_autotune(ctx, int(trial_steps), ctypes.byref(chosen)))
+    return chosen.value
+
+
 def flbm_last_error():
     return _lib.flbm_last_error().decode()
 
@@ -319,6 +336,17 @@ class Lattice:
 
     def sync(self):
         flbm_sync(self.ctx)
+
+    def autotune(self, trial_steps=10):
+        return flbm_autotune(self.ctx, trial_steps)
+
+    @property
+    def variant(self):
+        return flbm_get_step_variant(self.ctx)
+
+    @variant.setter
+    def variant(self, v):
+        flbm_set_step_variant(self.ctx, v)
 
     def close(self):
         if self.ctx:

@@ -52,8 +52,10 @@ def _err(a, b, lattice, rho0=1.0):
 
 
 def _run_pair(fl, oracle_mod, lattice, dims, lam, kBT, seed, steps, u0=(0, 0, 0), amp=0.0,
-              pseed=0, rho0=1.0, storage=0):
+              pseed=0, rho0=1.0, storage=0, variant=0):
     with fl.Lattice(lattice, dims, lam, kBT, rho0, seed, storage) as lat:
+        if variant:
+            lat.variant = variant
         lat.init_uniform(u0, amp, pseed)
         f0 = lat.populations()
         lat.step(steps)
@@ -72,12 +74,14 @@ def test_d2q9_64x64_fp64_config_parity(fl, oracle_mod):
     assert _err(fg, fo, 0) <= TOL
 
 
-def test_d3q27_drift_perturbed_ragged_box(fl, oracle_mod):
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+def test_d3q27_drift_perturbed_ragged_box(fl, oracle_mod, variant):
     # The headline workload's physics (drift (0.05, 0.02, 0), 1e-3 density perturbation,
-    # kBT = 1e-4, shear omega = 1.6) on a box spanning three x-blocks with a ragged tail.
+    # kBT = 1e-4, shear omega = 1.6) on a box spanning three x-blocks (one site per thread)
+    # or two (two sites per thread) with a ragged tail, for every step-kernel variant.
     lam = _lam(1, 1.6)
     f0, fg, fo = _run_pair(fl, oracle_mod, 1, (300, 7, 5), lam, 1e-4, 0, 100, (0.05, 0.02, 0.0),
-                           1e-3, 0)
+                           1e-3, 0, variant=variant)
     assert _err(fg, fo, 1) <= TOL
 
 
@@ -90,11 +94,23 @@ def test_d3q27_general_rates(fl, oracle_mod):
     assert _err(fg, fo, 1) <= TOL
 
 
-def test_d2q9_general_rates_ragged(fl, oracle_mod):
+@pytest.mark.parametrize("variant", [1, 3, 4])
+def test_d2q9_paper_rates(fl, oracle_mod, variant):
+    # D2Q9 with the paper's rates (L_4 = L_5 = omega, every other mode 1): the
+    # specialised path that forms only the shear central moments.
+    lam = _lam(0, 1.7)
+    f0, fg, fo = _run_pair(fl, oracle_mod, 0, (128, 21, 1), lam, 3e-4, 5, 100, (0.03, -0.02), 1e-3, 4,
+                           variant=variant)
+    assert _err(fg, fo, 0) <= TOL
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+def test_d2q9_general_rates_ragged(fl, oracle_mod, variant):
     rng = np.random.default_rng(6)
     lam = np.ones(9)
     lam[3:] = rng.uniform(0.3, 1.95, 6)
-    f0, fg, fo = _run_pair(fl, oracle_mod, 0, (200, 37, 1), lam, 5e-4, 9, 100, (-0.04, 0.03), 1e-3, 2)
+    f0, fg, fo = _run_pair(fl, oracle_mod, 0, (200, 37, 1), lam, 5e-4, 9, 100, (-0.04, 0.03), 1e-3, 2,
+                           variant=variant)
     assert _err(fg, fo, 0) <= TOL
 
 
@@ -137,6 +153,26 @@ def test_set_get_roundtrip_both_parities(fl, lattice, dims):
             sp = lat.sites_populations(sites)
             flat = back.reshape(q, -1)
             assert np.array_equal(sp, flat[:, sites].T)
+
+
+def test_autotune_leaves_the_state_unchanged(fl):
+    lam = _lam(1, 1.6)
+    with fl.Lattice(1, (64, 20, 18), lam, 1e-4, 1.0, 3) as lat:
+        lat.init_uniform((0.05, 0.02, 0.0), 1e-3, 0)
+        lat.step(3)
+        before = lat.populations()
+        chosen = lat.autotune(4)
+        assert chosen in (1, 2, 3, 4) and lat.variant == chosen
+        assert lat.step_count == 3
+        assert np.array_equal(lat.populations(), before)
+        lat.variant = 1
+        lat.step(5)
+        a = lat.populations()
+    with fl.Lattice(1, (64, 20, 18), lam, 1e-4, 1.0, 3) as lat:
+        lat.init_uniform((0.05, 0.02, 0.0), 1e-3, 0)
+        lat.variant = 1
+        lat.step(8)
+        assert np.array_equal(lat.populations(), a)
 
 
 def test_checkpoint_resume_is_bitwise(fl):
@@ -194,6 +230,9 @@ def test_sample_ring_matches_stats(fl):
 
 @pytest.mark.parametrize("storage,bits", [(1, 8), (2, 11)])
 def test_reduced_precision_one_step_bound(fl, oracle_mod, storage, bits):
+    # (nx = 70 and 20 with 16-bit storage: rows of 140 / 40 bytes, so the pipelined
+    # variant does not apply and the two-site kernel runs; the pipelined 16-bit path is
+    # covered by test_reduced_precision_pipelined.)
     # One step from the stored state: the only error beyond FP32 arithmetic is the
     # rounding of each stored deviation d* to the format (relative 2^-bits).
     for lattice, dims in ((0, (70, 9, 1)), (1, (20, 7, 6))):
@@ -244,3 +283,29 @@ def test_full_size_headline_sampled_sites(fl, oracle_mod):
             got = post[np.arange(27), np.arange(27)]
             worst = max(worst, float((np.abs(got - fstar) / w).max()))
     assert worst <= TOL
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_reduced_precision_pipelined_matches_pair_kernel(fl, storage):
+    # The pipelined kernels and the two-site kernels perform identical arithmetic (rolled
+    # or not); with 16-bit storage their stored results must agree bit for bit.
+    lam = _lam(1, 1.6)
+    out = []
+    for variant in (2, 3, 4):
+        with fl.Lattice(1, (64, 9, 7), lam, 1e-4, 1.0, 5, storage) as lat:
+            lat.variant = variant
+            assert lat.variant == variant
+            lat.init_uniform((0.05, 0.02, 0.0), 1e-3, 2)
+            lat.step(9)
+            out.append(lat.populations())
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
+
+
+@pytest.mark.parametrize("lattice,dims", [(0, (16, 12, 1)), (1, (8, 6, 5)), (1, (40, 3, 2))])
+def test_pipelined_small_rows_fewer_threads_than_populations(fl, oracle_mod, lattice, dims):
+    # Rows of 8 or 4 sites give blocks of 4 or 8 threads, fewer than Q bulk copies per tile.
+    lam = _lam(lattice, 1.6, 1.2)
+    f0, fg, fo = _run_pair(fl, oracle_mod, lattice, dims, lam, 1e-4, 12, 20, (0.02, 0.01, -0.01), 1e-3, 3,
+                           variant=4)
+    assert _err(fg, fo, lattice) <= TOL
