@@ -225,6 +225,95 @@ int flbm_sync(flbm_ctx *ctx);
 /* Message of the last failing call on this host thread (library-owned, never NULL). */
 const char *flbm_last_error(void);
 
+/*
+ * Batched ensembles: many independent periodic lattices, each with its own lattice
+ * type, size, relaxation rates, kBT, rho0 and noise seed, advanced together by one
+ * persistent kernel launch per flbm_batch_step call. Every lattice follows exactly the
+ * update of a single context with the same parameters (the same Philox stream keyed on
+ * its own seed, step and site); only the launch shape differs. The paper itself runs one
+ * lattice at a time; ensembles of independent runs are how its fluctuation statistics
+ * are gathered (Sec. III), which this form does in one launch.
+ *
+ * One spec per lattice (plain data, copied by flbm_batch_create):
+ *   lattice, dims, lambda, kBT, rho0, seed : as for flbm_create (lambda holds Q rates).
+ */
+typedef struct flbm_lattice_spec {
+  int32_t lattice;
+  int32_t reserved; /* must be 0 */
+  int64_t dims[3];
+  double lambda[27];
+  double kBT;
+  double rho0;
+  uint64_t seed;
+} flbm_lattice_spec;
+
+#define FLBM_BATCH_MAX_LATTICES 512
+
+/*
+ * flbm_batch_create - build n lattices (1 <= n <= FLBM_BATCH_MAX_LATTICES), all at rest
+ * and at step 0, with FP32 storage in one device allocation.
+ *   out         : receives the batch handle (release with flbm_batch_destroy).
+ *   specs       : n specs, host memory, read during the call only.
+ *   cuda_stream : cudaStream_t for all of the batch's work, or NULL for a stream the
+ *                 batch creates and owns. Graph capture needs a stream other than the
+ *                 legacy default stream.
+ * Errors: FLBM_EINVAL (bad spec: the message names its index), FLBM_ENOMEM, FLBM_ECUDA.
+ */
+int flbm_batch_create(flbm_batch **out, const flbm_lattice_spec *specs, int n, void *cuda_stream);
+void flbm_batch_destroy(flbm_batch *b);
+int flbm_batch_size(const flbm_batch *b);
+
+/*
+ * flbm_batch_lattice - borrowed context of lattice i (owned by the batch; valid until
+ * flbm_batch_destroy; NULL for a bad index). It shares the batch's stream, and the
+ * read and exchange calls work on it as on any context: flbm_stats, flbm_sample,
+ * flbm_fetch_samples, flbm_get_populations, flbm_set_populations, flbm_get_sites,
+ * flbm_save. flbm_init_uniform works while the batch is at step 0; flbm_load only
+ * restores a checkpoint taken at the batch's current step. flbm_step,
+ * flbm_set_step_variant and flbm_autotune return FLBM_ESTATE on it (the batch steps
+ * all of its lattices together), and flbm_destroy ignores it.
+ */
+flbm_ctx *flbm_batch_lattice(flbm_batch *b, int i);
+
+/*
+ * flbm_batch_step - enqueue n >= 0 steps of every lattice. Never synchronises. Two
+ * launch forms compute the same update (bitwise):
+ *   per-step (default): one plain launch per step over every tile of every lattice
+ *     (block = tile), then a one-thread update of the device step counter;
+ *   persistent: one cooperative launch of co-resident blocks that walk (step, tile)
+ *     items in order; a tile of lattice L waits (bounded) for all of L's tiles of the
+ *     step before, through per-lattice completion counters, instead of a grid barrier.
+ * Either way the n steps are captured once into a CUDA graph per (n, form, parity of the
+ * starting step) and replayed, where the stream allows capture. A bounded wait that
+ * gives up ends the persistent launch and makes the next flbm_batch_sync return
+ * FLBM_ETIMEOUT (the state is then not valid).
+ */
+int flbm_batch_step(flbm_batch *b, int64_t n);
+int64_t flbm_batch_get_step(const flbm_batch *b);
+
+/*
+ * Launch shape: threads per block (64, 128 or 256; every block takes tiles of
+ * 2 * threads sites; 0 restores the default, 128) and the launch form (persistent 1,
+ * per-step 0). flbm_batch_autotune times every (form, threads) pair over trial_steps
+ * steps (rounded up to even) on a copy of the state (restored afterwards, step count
+ * unchanged), keeps the fastest and returns it in *threads and *persistent (either may
+ * be NULL). Needs one extra copy of all populations in device memory while it runs.
+ * Synchronises.
+ */
+int flbm_batch_set_threads(flbm_batch *b, int threads);
+int flbm_batch_get_threads(const flbm_batch *b);
+int flbm_batch_set_persistent(flbm_batch *b, int persistent);
+int flbm_batch_get_persistent(const flbm_batch *b);
+int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads, int *persistent);
+
+/* 1 when the last flbm_batch_step replayed a captured graph, 0 when it launched
+ * directly (capture unavailable on this stream or runtime), -1 for a NULL handle. */
+int flbm_batch_uses_graph(const flbm_batch *b);
+
+/* Wait for the batch's stream; FLBM_ETIMEOUT if a bounded wait of the persistent form
+ * gave up (the flag is cleared), FLBM_ECUDA for an asynchronous device error. */
+int flbm_batch_sync(flbm_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

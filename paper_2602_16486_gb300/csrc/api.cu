@@ -46,6 +46,8 @@ struct flbm_ctx {
   bool shear = false;  // rates follow the paper's structure (collide.cuh, SHEAR)
   int *d_status = nullptr;  // device status word of the pipelined kernel
   StepArgs args{};
+  flbm_batch *owner = nullptr;  // set for a lattice of a batch (borrowed handle)
+  bool params_changed = false;  // a lattice of a batch reloaded its parameters
 };
 
 namespace {
@@ -347,7 +349,7 @@ int flbm_create(flbm_ctx **out, int lattice, const int64_t dims[3], const double
 }
 
 void flbm_destroy(flbm_ctx *ctx) {
-  if (!ctx) return;
+  if (!ctx || ctx->owner) return;
   DeviceGuard g(ctx->device);
   release(ctx);
 }
@@ -358,6 +360,8 @@ int flbm_init_uniform(flbm_ctx *c, const double u0[3], double amp, uint64_t pert
   for (int a = 0; a < c->D; ++a)
     if (!(std::fabs(u0[a]) < 1.0)) return fail(FLBM_EINVAL, "|u0[%d]| = %g must be < 1", a, u0[a]);
   if (!(amp >= 0.0 && amp < 1.0)) return fail(FLBM_EINVAL, "rho_perturb_amp = %g must lie in [0, 1)", amp);
+  if (c->owner && c->step != 0)
+    return fail(FLBM_ESTATE, "a lattice of a batch can be initialised only while the batch is at step 0");
   DeviceGuard g(c->device);
   FLBM_CUDA(launch_init(c->D, c->storage, c->f, c->N, int(c->dims[0]), int(c->dims[1]),
                         int(c->dims[2]), c->rho0, u0[0], u0[1], c->D == 3 ? u0[2] : 0.0, amp,
@@ -368,6 +372,7 @@ int flbm_init_uniform(flbm_ctx *c, const double u0[3], double amp, uint64_t pert
 
 int flbm_step(flbm_ctx *c, int64_t n) {
   if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (c->owner) return fail(FLBM_ESTATE, "a lattice of a batch advances with flbm_batch_step");
   if (n < 0) return fail(FLBM_EINVAL, "n = %lld must be >= 0", (long long)n);
   DeviceGuard g(c->device);
   const bool noise = c->kBT > 0.0;
@@ -570,6 +575,9 @@ int flbm_load(flbm_ctx *c, const void *host, size_t bytes) {
   if (bytes < sizeof(h) + h.payload_bytes) return fail(FLBM_EINVAL, "checkpoint blob truncated");
   const int st = check_params(h.lattice, h.lambda, h.kBT, h.rho0);
   if (st != FLBM_OK) return st;
+  if (c->owner && h.step != c->step)
+    return fail(FLBM_ESTATE, "checkpoint of step %lld, the batch is at step %lld", (long long)h.step,
+                (long long)c->step);
   DeviceGuard g(c->device);
   FLBM_CUDA(cudaMemcpyAsync(c->f, static_cast<const char *>(host) + sizeof(h), c->f_bytes,
                             cudaMemcpyHostToDevice, c->stream));
@@ -580,11 +588,13 @@ int flbm_load(flbm_ctx *c, const void *host, size_t bytes) {
   c->rho0 = h.rho0;
   for (int v = 0; v < c->Q; ++v) c->lambda[v] = (v <= c->D) ? 1.0 : h.lambda[v];
   fill_args(c);
+  c->params_changed = true;
   return FLBM_OK;
 }
 
 int flbm_set_step_variant(flbm_ctx *c, int variant) {
   if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (c->owner) return fail(FLBM_ESTATE, "a lattice of a batch has no step variant of its own");
   if (variant < kStepAuto || variant > kStepVariantMax)
     return fail(FLBM_EINVAL, "variant %d is not one of 0..%d", variant, int(kStepVariantMax));
   c->variant = variant;
@@ -595,6 +605,7 @@ int flbm_get_step_variant(const flbm_ctx *c) { return c ? resolve_variant(c) : -
 
 int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
   if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (c->owner) return fail(FLBM_ESTATE, "a lattice of a batch is tuned with flbm_batch_autotune");
   if (trial_steps < 2) return fail(FLBM_EINVAL, "trial_steps must be >= 2");
   DeviceGuard g(c->device);
   // Cache: one choice per (device, lattice, storage, nx parity, size class, noise).
@@ -687,6 +698,448 @@ int flbm_sync(flbm_ctx *c) {
 }
 
 const char *flbm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+// ---- batched ensembles -------------------------------------------------------------------
+// The batch owns one population allocation cut into its lattices' arrays (256-byte
+// aligned), one context per lattice (borrowed by the caller through flbm_batch_lattice,
+// sharing the batch's stream), the tile table and general-rate table of the persistent
+// kernel (batch.cu), its step counter, barrier words and status word.
+struct flbm_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void *pool = nullptr;
+  size_t pool_bytes = 0;
+  std::vector<flbm_ctx *> members;
+  std::vector<int> order;  // kernel table entry -> member (D3Q27 lattices first)
+  BatchGroup g3{}, g2{};   // the two lattice types' table entries and tiles
+  bool shear = true;       // every lattice follows the paper's rate structure
+  int threads = 128;       // block size; tiles hold 2 * threads sites
+  bool persistent = false;  // one cooperative launch per call (else one launch per step)
+  int grid = 0;            // co-resident blocks (cooperative launch)
+  int tiles_for = 0;       // block size the tiling was built for
+  int ntiles = 0;
+  float *d_rates = nullptr;  // om[27], phc[27] per lattice
+  long long *d_step = nullptr;
+  int *d_done = nullptr;           // per lattice: tiles finished in the running launch
+  unsigned int *d_exits = nullptr;  // blocks that have left the running launch
+  int *d_status = nullptr;
+  int64_t step = 0;
+  BatchArgs *args = nullptr;  // by-value kernel arguments (large: heap)
+  bool graphs_ok = true;      // capture worked (or was not tried yet)
+  bool last_graph = false;
+  std::map<int64_t, cudaGraphExec_t> graphs;  // per (n, form, start parity), current shape
+};
+
+namespace {
+
+constexpr int kBatchDefaultThreads = 128;
+
+void batch_drop_graphs(flbm_batch *b) {
+  for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+void batch_release(flbm_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graphs(b);
+  for (flbm_ctx *c : b->members) {
+    c->owner = nullptr;
+    release(c);
+  }
+  if (b->pool) cudaFree(b->pool);
+  if (b->d_rates) cudaFree(b->d_rates);
+  if (b->d_step) cudaFree(b->d_step);
+  if (b->d_done) cudaFree(b->d_done);
+  if (b->d_exits) cudaFree(b->d_exits);
+  if (b->d_status) cudaFree(b->d_status);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b->args;
+  delete b;
+}
+
+// Kernel arguments from the lattices' contexts: geometry, keys, the paper-structure
+// triple (sqrt kBT, 1 - L_shear, phc_shear) and the general-rate table.
+int batch_params(flbm_batch *b) {
+  const int n = int(b->members.size());
+  std::vector<float> rates(size_t(n) * 54, 0.0f);
+  b->shear = true;
+  for (int i = 0; i < n; ++i) {
+    flbm_ctx *c = b->members[size_t(b->order[size_t(i)])];
+    const StepArgs &a = c->args;
+    BatchLattice &L = b->args->lats[i];
+    L.f = c->f;
+    L.plane = uint32_t(c->N);
+    L.nx = a.nx;
+    L.ny = a.ny;
+    L.nz = a.nz;
+    L.D = c->D;
+    L.rho0 = a.rho0;
+    L.key0 = a.key0;
+    L.key1 = a.key1;
+    const int ref = c->D == 3 ? 7 : 5;  // a shear mode with b = 1/9
+    L.sqrt_kbt = float(std::sqrt(c->kBT));
+    L.om_shear = a.om[ref];
+    L.phc_shear = a.phc[ref];
+    for (int v = 0; v < 27; ++v) {
+      rates[size_t(i) * 54 + size_t(v)] = a.om[v];
+      rates[size_t(i) * 54 + 27 + size_t(v)] = a.phc[v];
+    }
+    // The shear form needs the paper's structure and one rate shared by the shear modes.
+    bool ok = c->shear;
+    if (c->D == 3)
+      ok = ok && a.om[8] == a.om[7] && a.om[9] == a.om[7] && a.phc[8] == a.phc[7] && a.phc[9] == a.phc[7];
+    else
+      ok = ok && a.om[4] == a.om[5] && a.phc[4] == 2.0f * a.phc[5];
+    if (!ok) b->shear = false;
+    c->params_changed = false;
+  }
+  FLBM_CUDA(cudaMemcpyAsync(b->d_rates, rates.data(), rates.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            b->stream));
+  FLBM_CUDA(cudaStreamSynchronize(b->stream));  // `rates` is a local
+  return FLBM_OK;
+}
+
+// Tiling for the block size b->threads (tiles of 2 * threads sites, never spanning
+// lattices; lattice i owns tiles [tile0_i, tile0_{i+1})) and the grid of co-resident
+// blocks.
+int batch_shape(flbm_batch *b) {
+  if (b->tiles_for == b->threads) return FLBM_OK;
+  const long long span = 2LL * b->threads;
+  long long total = 0;
+  const int nl = int(b->members.size());
+  int n3 = 0;  // table entries 0 .. n3-1 are the D3Q27 lattices
+  while (n3 < nl && b->members[size_t(b->order[size_t(n3)])]->D == 3) ++n3;
+  long long tiles3 = 0;
+  for (int i = 0; i < nl; ++i) {
+    if (i == n3) tiles3 = total;
+    b->args->lats[i].tile0 = int(total);
+    total += (b->members[size_t(b->order[size_t(i)])]->N + span - 1) / span;
+    if (total > 0x3fffffffLL) return fail(FLBM_EINVAL, "too many tiles");
+  }
+  if (n3 == nl) tiles3 = total;
+  b->g3 = BatchGroup{0, n3, 0, int(tiles3)};
+  b->g2 = BatchGroup{n3, nl, int(tiles3), int(total - tiles3)};
+  FLBM_CUDA(cudaStreamSynchronize(b->stream));
+  batch_drop_graphs(b);
+  b->tiles_for = 0;
+  b->ntiles = int(total);
+  int per_sm = 0, sms = 0;
+  FLBM_CUDA(batch_max_blocks(b->shear, b->threads, &per_sm));
+  FLBM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  if (per_sm < 1) return fail(FLBM_ECUDA, "the batch kernel cannot be resident with %d threads", b->threads);
+  const long long g = (long long)per_sm * sms;
+  b->grid = int(g < b->ntiles ? g : b->ntiles);
+  b->tiles_for = b->threads;
+  return FLBM_OK;
+}
+
+// Enqueue n steps: the persistent form resets the completion counters and makes one
+// cooperative launch; the per-step form makes n plain launches and a counter update.
+int batch_enqueue(flbm_batch *b, int64_t n) {
+  b->args->rates = b->d_rates;
+  b->args->nlat = int(b->members.size());
+  b->args->ntiles = b->ntiles;
+  b->args->span = 2 * b->threads;
+  b->args->nsteps = int(n);
+  b->args->step_counter = b->d_step;
+  b->args->done = b->d_done;
+  b->args->exits = b->d_exits;
+  b->args->status = b->d_status;
+  if (!b->persistent) {
+    FLBM_CUDA(launch_batch_steps(b->shear, int(b->step & 1), *b->args, b->g3, b->g2, int(n), b->threads,
+                                 b->stream));
+    return FLBM_OK;
+  }
+  FLBM_CUDA(cudaMemsetAsync(b->d_done, 0, b->members.size() * sizeof(int), b->stream));
+  FLBM_CUDA(cudaMemsetAsync(b->d_exits, 0, sizeof(unsigned int), b->stream));
+  FLBM_CUDA(launch_batch(b->shear, *b->args, b->grid, b->threads, b->stream));
+  return FLBM_OK;
+}
+
+// The captured graph of n steps in the current form, or nullptr where capture is
+// unavailable.
+cudaGraphExec_t batch_graph(flbm_batch *b, int64_t n) {
+  if (!b->graphs_ok) return nullptr;
+  const int64_t key = n * 4 + (b->persistent ? 2 : int64_t(b->step & 1));
+  auto it = b->graphs.find(key);
+  if (it != b->graphs.end()) return it->second;
+  if (b->graphs.size() >= 16) batch_drop_graphs(b);
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    b->graphs_ok = false;
+    return nullptr;
+  }
+  const int st = batch_enqueue(b, n);
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (st == FLBM_OK && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+    cudaGraphDestroy(g);
+    b->graphs[key] = exec;
+    return exec;
+  }
+  cudaGetLastError();
+  if (g) cudaGraphDestroy(g);
+  b->graphs_ok = false;
+  return nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int flbm_batch_create(flbm_batch **out, const flbm_lattice_spec *specs, int n, void *cuda_stream) {
+  if (!out) return fail(FLBM_EINVAL, "out is NULL");
+  if (!specs) return fail(FLBM_EINVAL, "specs is NULL");
+  if (n < 1 || n > kBatchMaxLattices)
+    return fail(FLBM_EINVAL, "n = %d must lie in [1, %d]", n, int(kBatchMaxLattices));
+  static_assert(FLBM_BATCH_MAX_LATTICES == kBatchMaxLattices, "header and kernel bounds differ");
+  std::vector<size_t> offset(static_cast<size_t>(n), 0);
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    const flbm_lattice_spec &s = specs[i];
+    if (s.reserved != 0) return fail(FLBM_EINVAL, "specs[%d].reserved must be 0", i);
+    int st = check_geometry(s.lattice, s.dims, FLBM_FP32);
+    if (st == FLBM_OK) st = check_params(s.lattice, s.lambda, s.kBT, s.rho0);
+    if (st != FLBM_OK) return fail(st, "specs[%d]: %s", i, g_last_error.c_str());
+    offset[size_t(i)] = total;
+    total += (flbm_required_bytes(s.lattice, s.dims, FLBM_FP32) + 255) / 256 * 256;
+  }
+  int dev = 0;
+  FLBM_CUDA(cudaGetDevice(&dev));
+  int coop = 0;
+  FLBM_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return fail(FLBM_ECUDA, "device %d does not support cooperative launches", dev);
+
+  flbm_batch *b = new (std::nothrow) flbm_batch();
+  if (!b) return fail(FLBM_ENOMEM, "host allocation failed");
+  b->args = new (std::nothrow) BatchArgs();
+  if (!b->args) {
+    delete b;
+    return fail(FLBM_ENOMEM, "host allocation failed");
+  }
+  b->device = dev;
+  b->threads = kBatchDefaultThreads;
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      batch_release(b);
+      return fail(FLBM_ECUDA, "cudaStreamCreateWithFlags: %s", cudaGetErrorString(e));
+    }
+    b->own_stream = true;
+  }
+  e = cudaMalloc(&b->pool, total);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_rates, size_t(n) * 54 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_step, sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_done, size_t(n) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_exits, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    batch_release(b);
+    return fail(FLBM_ENOMEM, "cannot allocate %zu bytes of batch memory", total);
+  }
+  b->pool_bytes = total;
+  if (cudaMemsetAsync(b->d_step, 0, sizeof(long long), b->stream) != cudaSuccess ||
+      cudaMemsetAsync(b->d_done, 0, size_t(n) * sizeof(int), b->stream) != cudaSuccess ||
+      cudaMemsetAsync(b->d_exits, 0, sizeof(unsigned int), b->stream) != cudaSuccess ||
+      cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream) != cudaSuccess) {
+    batch_release(b);
+    return fail(FLBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  for (int i = 0; i < n; ++i) {
+    const flbm_lattice_spec &s = specs[i];
+    flbm_ctx *c = nullptr;
+    const size_t need = flbm_required_bytes(s.lattice, s.dims, FLBM_FP32);
+    const int st = flbm_create_ex(&c, s.lattice, s.dims, s.lambda, s.kBT, s.rho0, s.seed, FLBM_FP32, b->stream,
+                                  static_cast<char *>(b->pool) + offset[size_t(i)], need);
+    if (st != FLBM_OK) {
+      const std::string msg = g_last_error;
+      batch_release(b);
+      return fail(st, "lattice %d: %s", i, msg.c_str());
+    }
+    c->owner = b;
+    c->variant = kStepPair;
+    b->members.push_back(c);
+  }
+  for (int i = 0; i < n; ++i)
+    if (b->members[size_t(i)]->D == 3) b->order.push_back(i);
+  for (int i = 0; i < n; ++i)
+    if (b->members[size_t(i)]->D == 2) b->order.push_back(i);
+  int st = batch_params(b);
+  if (st == FLBM_OK) st = batch_shape(b);
+  if (st != FLBM_OK) {
+    const std::string msg = g_last_error;
+    batch_release(b);
+    return fail(st, "%s", msg.c_str());
+  }
+  *out = b;
+  return FLBM_OK;
+}
+
+void flbm_batch_destroy(flbm_batch *b) {
+  if (!b) return;
+  DeviceGuard g(b->device);
+  batch_release(b);
+}
+
+int flbm_batch_size(const flbm_batch *b) { return b ? int(b->members.size()) : -1; }
+
+flbm_ctx *flbm_batch_lattice(flbm_batch *b, int i) {
+  if (!b || i < 0 || i >= int(b->members.size())) {
+    fail(FLBM_EINVAL, "no lattice %d in this batch", i);
+    return nullptr;
+  }
+  return b->members[size_t(i)];
+}
+
+int flbm_batch_step(flbm_batch *b, int64_t n) {
+  if (!b) return fail(FLBM_EINVAL, "batch is NULL");
+  if (n < 0 || n > 0x7fffffff) return fail(FLBM_EINVAL, "n = %lld must lie in [0, 2^31)", (long long)n);
+  if (n == 0) return FLBM_OK;
+  DeviceGuard g(b->device);
+  bool changed = false;
+  for (flbm_ctx *c : b->members) changed = changed || c->params_changed;
+  if (changed) {
+    int st = batch_params(b);
+    if (st != FLBM_OK) return st;
+    batch_drop_graphs(b);
+    b->tiles_for = 0;  // the kernel form (shear) may have changed: new grid
+  }
+  int st = batch_shape(b);
+  if (st != FLBM_OK) return st;
+  cudaGraphExec_t exec = batch_graph(b, n);
+  b->last_graph = exec != nullptr;
+  if (exec) {
+    FLBM_CUDA(cudaGraphLaunch(exec, b->stream));
+  } else {
+    st = batch_enqueue(b, n);
+    if (st != FLBM_OK) return st;
+  }
+  b->step += n;
+  for (flbm_ctx *c : b->members) c->step = b->step;
+  return FLBM_OK;
+}
+
+int64_t flbm_batch_get_step(const flbm_batch *b) { return b ? b->step : -1; }
+
+int flbm_batch_set_threads(flbm_batch *b, int threads) {
+  if (!b) return fail(FLBM_EINVAL, "batch is NULL");
+  if (threads == 0) threads = kBatchDefaultThreads;
+  if (threads != 64 && threads != 128 && threads != 256)
+    return fail(FLBM_EINVAL, "threads = %d must be 64, 128 or 256 (or 0)", threads);
+  if (threads != b->threads) batch_drop_graphs(b);
+  b->threads = threads;
+  return FLBM_OK;
+}
+
+int flbm_batch_set_persistent(flbm_batch *b, int persistent) {
+  if (!b) return fail(FLBM_EINVAL, "batch is NULL");
+  if (persistent != 0 && persistent != 1) return fail(FLBM_EINVAL, "persistent must be 0 or 1");
+  b->persistent = persistent == 1;
+  return FLBM_OK;
+}
+
+int flbm_batch_get_persistent(const flbm_batch *b) { return b ? (b->persistent ? 1 : 0) : -1; }
+
+int flbm_batch_get_threads(const flbm_batch *b) { return b ? b->threads : -1; }
+
+int flbm_batch_uses_graph(const flbm_batch *b) { return b ? (b->last_graph ? 1 : 0) : -1; }
+
+int flbm_batch_sync(flbm_batch *b) {
+  if (!b) return fail(FLBM_EINVAL, "batch is NULL");
+  DeviceGuard g(b->device);
+  FLBM_CUDA(cudaStreamSynchronize(b->stream));
+  int h = 0;
+  FLBM_CUDA(cudaMemcpy(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    FLBM_CUDA(cudaMemset(b->d_status, 0, sizeof(int)));
+    return fail(FLBM_ETIMEOUT, "a bounded wait of the batch kernel gave up; the state is not valid");
+  }
+  return FLBM_OK;
+}
+
+int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads_out, int *persistent_out) {
+  if (!b) return fail(FLBM_EINVAL, "batch is NULL");
+  if (trial_steps < 2) return fail(FLBM_EINVAL, "trial_steps must be >= 2");
+  DeviceGuard g(b->device);
+  void *backup = nullptr;
+  if (cudaMalloc(&backup, b->pool_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FLBM_ENOMEM, "cannot allocate %zu bytes for the autotuner's state copy", b->pool_bytes);
+  }
+  const int64_t step0 = b->step;
+  const long long step0_dev = (long long)step0;
+  const int saved_t = b->threads;
+  const bool saved_p = b->persistent;
+  int best_t = saved_t, st = FLBM_OK;
+  bool best_p = saved_p;
+  float best = 1e30f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  do {
+    if (cudaMemcpyAsync(backup, b->pool, b->pool_bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      st = fail(FLBM_ECUDA, "autotune set-up: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    for (int p = 0; p < 2 && st == FLBM_OK; ++p) {
+      for (int t : {64, 128, 256}) {
+        b->threads = t;
+        b->persistent = p == 1;
+        // warm-up and capture of the timed shape (an even count keeps the start parity
+        // of the timed call, so that it replays the captured graph)
+        const int64_t nt = trial_steps + (trial_steps & 1);
+        if ((st = flbm_batch_step(b, 2)) != FLBM_OK) break;
+        if ((st = flbm_batch_step(b, nt)) != FLBM_OK) break;
+        cudaEventRecord(e0, b->stream);
+        if ((st = flbm_batch_step(b, nt)) != FLBM_OK) break;
+        cudaEventRecord(e1, b->stream);
+        if ((st = flbm_batch_sync(b)) != FLBM_OK) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_t = t;
+          best_p = p == 1;
+        }
+        b->step = step0;
+        for (flbm_ctx *c : b->members) c->step = step0;
+        if (cudaMemcpyAsync(b->pool, backup, b->pool_bytes, cudaMemcpyDeviceToDevice, b->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(b->d_step, &step0_dev, sizeof(long long), cudaMemcpyHostToDevice, b->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(b->stream) != cudaSuccess) {
+          st = fail(FLBM_ECUDA, "autotune restore failed");
+          break;
+        }
+      }
+    }
+  } while (false);
+  cudaStreamSynchronize(b->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(backup);
+  b->step = step0;
+  for (flbm_ctx *c : b->members) c->step = step0;
+  if (st != FLBM_OK) {
+    b->threads = saved_t;
+    b->persistent = saved_p;
+    return st;
+  }
+  if (best_t != b->threads) batch_drop_graphs(b);
+  b->threads = best_t;
+  b->persistent = best_p;
+  if (threads_out) *threads_out = best_t;
+  if (persistent_out) *persistent_out = best_p ? 1 : 0;
+  return FLBM_OK;
+}
 
 }  // extern "C"
 

@@ -17,17 +17,57 @@
 
 namespace flbm {
 
+// ---- relaxation rates and noise amplitudes, as the collision reads them --------------
+// ArrayRates: om_v = 1 - L_v and phc_v = sqrt(kBT L_v (2 - L_v) b_v / cs^2) per mode, from
+// a kernel-argument array (constant bank).
+struct ArrayRates {
+  const float *om_, *phc_;
+  __device__ __forceinline__ float om(int v) const { return om_[v]; }
+  __device__ __forceinline__ float phc(int v) const { return phc_[v]; }
+};
+
+// sqrt(b_v / cs^2) = sqrt(3 b_v) of the modes, b_v the product of the 1-D norms
+// (1, 1/3, 2/9) over the tensor orders (D2Q9 modes 3 and 4: 2 * 2/9). Compile-time.
+__host__ __device__ constexpr double csqrt(double x) {
+  double r = x > 1.0 ? x : 1.0;
+  for (int i = 0; i < 64; ++i) r = 0.5 * (r + x / r);
+  return r;
+}
+__host__ __device__ constexpr double bnorm1(int order) { return order == 0 ? 1.0 : order == 1 ? 1.0 / 3.0 : 2.0 / 9.0; }
+template <int D>
+__host__ __device__ constexpr float noise_unit(int v) {
+  return D == 3 ? (float)csqrt(3.0 * bnorm1(d3q27_mode_tensor(v) % 3) * bnorm1((d3q27_mode_tensor(v) / 3) % 3) *
+                               bnorm1(d3q27_mode_tensor(v) / 9))
+         : (v == 3 || v == 4) ? (float)csqrt(3.0 * 2.0 * bnorm1(2))
+                              : (float)csqrt(3.0 * bnorm1(d2q9_mode_tensor(v) % 3) * bnorm1(d2q9_mode_tensor(v) / 3));
+}
+
+// ShearRates: the paper's structure (L_v = 1 except the shear modes, which share one
+// rate): om = 0 and phc_v = sqrt(kBT) sqrt(3 b_v) off the shear modes, om_sh and phc_sh
+// on them. phc_sh is the amplitude of a shear mode with b = 1/9 (D3Q27 v = 7..9, D2Q9
+// v = 5); D2Q9 mode 4 has b = 4/9 and so twice that amplitude (an exact scaling). Three
+// numbers per lattice.
+template <int D>
+struct ShearRates {
+  float sqrt_kbt, om_sh, phc_sh;
+  __device__ __forceinline__ static bool is_shear(int v) { return D == 3 ? (v >= 7 && v <= 9) : (v == 4 || v == 5); }
+  __device__ __forceinline__ float om(int v) const { return is_shear(v) ? om_sh : 0.0f; }
+  __device__ __forceinline__ float phc(int v) const {
+    return is_shear(v) ? ((D == 2 && v == 4) ? 2.0f * phc_sh : phc_sh) : sqrt_kbt * noise_unit<D>(v);
+  }
+};
+
 // D3Q27: adds phi_v eta_v (eta already scaled by sqrt(rho)) to the four modes that
 // Philox block BLK feeds, v = 4 + 4 BLK + j (j < 4, v < 27).
-template <int BLK, typename T>
-__device__ __forceinline__ void add_noise_block(T (&F)[3][3][3], const float *phc, const T (&z)[4]) {
+template <int BLK, typename T, typename R>
+__device__ __forceinline__ void add_noise_block(T (&F)[3][3][3], const R &rates, const T (&z)[4]) {
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int v = 4 + 4 * BLK + j;
     if (v < 27) {
       const int t = d3q27_mode_tensor(v);
       T &k = F[t / 9][(t / 3) % 3][t % 3];
-      k = vfma(splat<T>(phc[v]), z[j], k);
+      k = vfma(splat<T>(rates.phc(v)), z[j], k);
     }
   }
 }
@@ -40,11 +80,10 @@ __device__ __forceinline__ void add_noise_block(T (&F)[3][3][3], const float *ph
 // and II-B). Then k*_v = phi_v eta_v needs no pre-collision value, and only the shear
 // central moments are formed, directly as k_ab = r_ab - rho u_a u_b (Sec. II-C prints
 // k7-k9 in this form) instead of through the full velocity shift.
-template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false>
-__device__ __forceinline__ void collide_tile(T (&F)[3][3][3], float rho0, const float *om,
-                                             const float *phc, uint32_t site0, uint32_t step_lo,
-                                             uint32_t step_hi, const uint32_t *ks0,
-                                             const uint32_t *ks1) {
+template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false, typename R, typename K>
+__device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const R &rates, uint32_t site0,
+                                              uint32_t step_lo, uint32_t step_hi, const K &keys,
+                                              uint32_t dsite = 1) {
   T drho, rho, ux, uy, uz;
   if (SHEAR) {
     site_macros<D>(F, rho0, drho, rho, ux, uy, uz);
@@ -68,43 +107,43 @@ __device__ __forceinline__ void collide_tile(T (&F)[3][3][3], float rho0, const 
         const int t = d3q27_mode_tensor(v);
         F[t / 9][(t / 3) % 3][t % 3] = splat<T>(0.0f);
       }
-      F[0][1][1] = vmul(splat<T>(om[7]), kxy);
-      F[1][0][1] = vmul(splat<T>(om[8]), kxz);
-      F[1][1][0] = vmul(splat<T>(om[9]), kyz);
+      F[0][1][1] = vmul(splat<T>(rates.om(7)), kxy);
+      F[1][0][1] = vmul(splat<T>(rates.om(8)), kxz);
+      F[1][1][0] = vmul(splat<T>(rates.om(9)), kyz);
     } else {
 #pragma unroll
       for (int v = 4; v < 27; ++v) {
         const int t = d3q27_mode_tensor(v);
         T &k = F[t / 9][(t / 3) % 3][t % 3];
-        k = vmul(splat<T>(om[v]), k);
+        k = vmul(splat<T>(rates.om(v)), k);
       }
     }
     if (NOISE && ROLLED) {
 #pragma unroll 1
       for (int blk = 0; blk < 6; ++blk) {
         T z[4];
-        normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, ks0, ks1, srho, z);
+        normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, keys, srho, z, dsite);
         switch (blk) {  // block-uniform branch: modes 4 + 4 blk .. 7 + 4 blk
-          case 0: add_noise_block<0>(F, phc, z); break;
-          case 1: add_noise_block<1>(F, phc, z); break;
-          case 2: add_noise_block<2>(F, phc, z); break;
-          case 3: add_noise_block<3>(F, phc, z); break;
-          case 4: add_noise_block<4>(F, phc, z); break;
-          default: add_noise_block<5>(F, phc, z); break;
+          case 0: add_noise_block<0>(F, rates, z); break;
+          case 1: add_noise_block<1>(F, rates, z); break;
+          case 2: add_noise_block<2>(F, rates, z); break;
+          case 3: add_noise_block<3>(F, rates, z); break;
+          case 4: add_noise_block<4>(F, rates, z); break;
+          default: add_noise_block<5>(F, rates, z); break;
         }
       }
     } else if (NOISE) {
 #pragma unroll
       for (int blk = 0; blk < 6; ++blk) {
         T z[4];
-        normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, ks0, ks1, srho, z);
+        normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, keys, srho, z, dsite);
         switch (blk) {
-          case 0: add_noise_block<0>(F, phc, z); break;
-          case 1: add_noise_block<1>(F, phc, z); break;
-          case 2: add_noise_block<2>(F, phc, z); break;
-          case 3: add_noise_block<3>(F, phc, z); break;
-          case 4: add_noise_block<4>(F, phc, z); break;
-          default: add_noise_block<5>(F, phc, z); break;
+          case 0: add_noise_block<0>(F, rates, z); break;
+          case 1: add_noise_block<1>(F, rates, z); break;
+          case 2: add_noise_block<2>(F, rates, z); break;
+          case 3: add_noise_block<3>(F, rates, z); break;
+          case 4: add_noise_block<4>(F, rates, z); break;
+          default: add_noise_block<5>(F, rates, z); break;
         }
       }
     }
@@ -119,28 +158,28 @@ __device__ __forceinline__ void collide_tile(T (&F)[3][3][3], float rho0, const 
       // other non-conserved modes restart from k^eq = 0.
       const T nrho = vmul(splat<T>(-1.0f), rho);
       const T d2 = vsub(vmul(ux, ux), vmul(uy, uy));
-      k4 = vmul(splat<T>(om[4]), vfma(nrho, d2, vsub(F[1][0][2], F[1][2][0])));
-      k5 = vmul(splat<T>(om[5]), vfma(vmul(nrho, ux), uy, F[1][1][1]));
+      k4 = vmul(splat<T>(rates.om(4)), vfma(nrho, d2, vsub(F[1][0][2], F[1][2][0])));
+      k5 = vmul(splat<T>(rates.om(5)), vfma(vmul(nrho, ux), uy, F[1][1][1]));
       k3 = k6 = k7 = k8 = splat<T>(0.0f);
     } else {
       const T kxx = F[1][0][2], kyy = F[1][2][0];
-      k3 = vmul(splat<T>(om[3]), vadd(kxx, kyy));
-      k4 = vmul(splat<T>(om[4]), vsub(kxx, kyy));
-      k5 = vmul(splat<T>(om[5]), F[1][1][1]);
-      k6 = vmul(splat<T>(om[6]), F[1][1][2]);
-      k7 = vmul(splat<T>(om[7]), F[1][2][1]);
-      k8 = vmul(splat<T>(om[8]), F[1][2][2]);
+      k3 = vmul(splat<T>(rates.om(3)), vadd(kxx, kyy));
+      k4 = vmul(splat<T>(rates.om(4)), vsub(kxx, kyy));
+      k5 = vmul(splat<T>(rates.om(5)), F[1][1][1]);
+      k6 = vmul(splat<T>(rates.om(6)), F[1][1][2]);
+      k7 = vmul(splat<T>(rates.om(7)), F[1][2][1]);
+      k8 = vmul(splat<T>(rates.om(8)), F[1][2][2]);
     }
     if (NOISE) {
       T z0[4], z1[4];
-      normals4_scaled<T>(site0, step_lo, step_hi, 0u, ks0, ks1, srho, z0);
-      normals4_scaled<T>(site0, step_lo, step_hi, 1u, ks0, ks1, srho, z1);
-      k3 = vfma(splat<T>(phc[3]), z0[0], k3);
-      k4 = vfma(splat<T>(phc[4]), z0[1], k4);
-      k5 = vfma(splat<T>(phc[5]), z0[2], k5);
-      k6 = vfma(splat<T>(phc[6]), z0[3], k6);
-      k7 = vfma(splat<T>(phc[7]), z1[0], k7);
-      k8 = vfma(splat<T>(phc[8]), z1[1], k8);
+      normals4_scaled<T>(site0, step_lo, step_hi, 0u, keys, srho, z0, dsite);
+      normals4_scaled<T>(site0, step_lo, step_hi, 1u, keys, srho, z1, dsite);
+      k3 = vfma(splat<T>(rates.phc(3)), z0[0], k3);
+      k4 = vfma(splat<T>(rates.phc(4)), z0[1], k4);
+      k5 = vfma(splat<T>(rates.phc(5)), z0[2], k5);
+      k6 = vfma(splat<T>(rates.phc(6)), z0[3], k6);
+      k7 = vfma(splat<T>(rates.phc(7)), z1[0], k7);
+      k8 = vfma(splat<T>(rates.phc(8)), z1[1], k8);
     }
     const T h = splat<T>(0.5f);
     F[1][0][2] = vmul(h, vadd(k3, k4));
@@ -156,6 +195,16 @@ __device__ __forceinline__ void collide_tile(T (&F)[3][3][3], float rho0, const 
   tile_shift_inv<D>(F, ux, uy, uz);
   mom<D>(F, 0, 0, 0) = drho;
   tile_raw_inv<D>(F);
+}
+
+// The collision with per-mode arrays om_v, phc_v (kernel arguments).
+template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false>
+__device__ __forceinline__ void collide_tile(T (&F)[3][3][3], float rho0, const float *om,
+                                             const float *phc, uint32_t site0, uint32_t step_lo,
+                                             uint32_t step_hi, const uint32_t *ks0,
+                                             const uint32_t *ks1) {
+  collide_rates<D, NOISE, T, ROLLED, SHEAR>(F, rho0, ArrayRates{om, phc}, site0, step_lo, step_hi,
+                                            KeyTable{ks0, ks1});
 }
 
 }  // namespace flbm

@@ -27,6 +27,42 @@ struct StepArgs {
   float phc[27];      // sqrt(kBT Lambda_v (2 - Lambda_v) b_v / cs^2); phi_v = sqrt(rho) phc_v
 };
 
+// ---- batched ensembles (batch.cu) ----------------------------------------------------
+constexpr int kBatchMaxThreads = 256;  // largest tile: 512 sites (two per thread)
+
+constexpr int kBatchMaxLattices = 512;  // bound of the by-value lattice table below
+
+struct BatchLattice {  // one lattice of a batch (FP32 storage); lives in the kernel arguments
+  void *f;
+  uint32_t plane;  // nx * ny * nz (< 2^32)
+  int nx, ny, nz, D;
+  float rho0;
+  uint32_t key0, key1;                  // noise key (seed)
+  float sqrt_kbt, om_shear, phc_shear;  // rates in the paper's structure (ShearRates)
+  int tile0;                            // index of the lattice's first tile
+};
+struct BatchArgs {
+  const float *rates;        // general rates: om[27] then phc[27] per lattice (device)
+  int nlat, ntiles, nsteps;  // lattices, tiles (all lattices), steps of this launch
+  int span;                  // sites per tile (2 * threads per block)
+  long long *step_counter;   // device: completed steps of every lattice
+  int *done;                 // device, one per lattice, zero at launch: tiles finished
+  unsigned int *exits;       // device, zero at launch: blocks that have left
+  int *status;               // nonzero after a bounded wait gave up
+  BatchLattice lats[kBatchMaxLattices];
+};
+cudaError_t batch_max_blocks(bool shear, int threads, int *blocks_per_sm);
+cudaError_t launch_batch(bool shear, const BatchArgs &a, int grid, int threads, cudaStream_t s);
+// The lattices of one type: table entries [lat_lo, lat_hi) owning tiles
+// [tile0, tile0 + ntiles).
+struct BatchGroup {
+  int lat_lo, lat_hi, tile0, ntiles;
+};
+// n steps as plain launches (per step one launch per lattice type, block = tile), then
+// the step-counter update.
+cudaError_t launch_batch_steps(bool shear, int parity0, const BatchArgs &a, const BatchGroup &g3,
+                               const BatchGroup &g2, int n, int threads, cudaStream_t s);
+
 // Statistics accumulators, in doubles: see stats.cu for the layout.
 int stats_nacc(int Q);
 inline int stats_record_len(int Q) { return stats_nacc(Q) + 1; }  // + non-finite count

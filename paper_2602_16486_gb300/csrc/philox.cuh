@@ -59,15 +59,28 @@ __device__ __forceinline__ Normals4 normals4(uint32_t site, uint32_t step_lo, ui
   return n;
 }
 
-// Philox4x32-10 with the round keys precomputed (k0[r] = key0 + r W0, k1[r] = key1 +
-// r W1); the 64-bit products give each round's high and low words in one multiply.
-__device__ __forceinline__ uint4 philox4x32_10_ks(uint4 ctr, const uint32_t *k0, const uint32_t *k1) {
+// Round keys of Philox4x32-10: key + r (W0, W1). KeyTable reads them precomputed (kernel
+// arguments, constant bank); KeyBase forms them from the key (per-lattice keys in memory).
+struct KeyTable {
+  const uint32_t *t0, *t1;
+  __device__ __forceinline__ uint32_t k0(int r) const { return t0[r]; }
+  __device__ __forceinline__ uint32_t k1(int r) const { return t1[r]; }
+};
+struct KeyBase {
+  uint32_t b0, b1;
+  __device__ __forceinline__ uint32_t k0(int r) const { return b0 + (uint32_t)r * 0x9E3779B9u; }
+  __device__ __forceinline__ uint32_t k1(int r) const { return b1 + (uint32_t)r * 0xBB67AE85u; }
+};
+
+// Philox4x32-10; the 64-bit products give each round's high and low words in one multiply.
+template <typename K>
+__device__ __forceinline__ uint4 philox4x32_10_ks(uint4 ctr, const K &keys) {
 #pragma unroll
   for (int round = 0; round < 10; ++round) {
     const unsigned long long p0 = (unsigned long long)0xD2511F53u * ctr.x;
     const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * ctr.z;
-    ctr = make_uint4((uint32_t)(p1 >> 32) ^ ctr.y ^ k0[round], (uint32_t)p1,
-                     (uint32_t)(p0 >> 32) ^ ctr.w ^ k1[round], (uint32_t)p0);
+    ctr = make_uint4((uint32_t)(p1 >> 32) ^ ctr.y ^ keys.k0(round), (uint32_t)p1,
+                     (uint32_t)(p0 >> 32) ^ ctr.w ^ keys.k1(round), (uint32_t)p0);
   }
   return ctr;
 }
@@ -117,19 +130,19 @@ __device__ __forceinline__ void bm_finish(float s, float c, uint32_t half, float
   zb = rr * s;
 }
 
-// Four normals of Philox block `blk` for each lane's site (lane l: site0 + l), each
-// multiplied by `scale` of its lane (the caller's sqrt(rho)).
-template <typename T>
+// Four normals of Philox block `blk` for each lane's site (lane l: site0 + l * dsite),
+// each multiplied by `scale` of its lane (the caller's sqrt(rho)).
+template <typename T, typename K>
 __device__ __forceinline__ void normals4_scaled(uint32_t site0, uint32_t step_lo, uint32_t step_hi,
-                                                uint32_t blk, const uint32_t *k0, const uint32_t *k1,
-                                                T scale, T (&z)[4]) {
+                                                uint32_t blk, const K &keys, T scale, T (&z)[4],
+                                                uint32_t dsite = 1) {
   constexpr int L = Lanes<T>::n;
   float rad[L][2], ang_l[L][2];
   uint32_t hturn[L][2];
   uint32_t wav[L][2];
 #pragma unroll
   for (int l = 0; l < L; ++l) {
-    const uint4 w = philox4x32_10_ks(make_uint4(site0 + l, step_lo, step_hi, blk), k0, k1);
+    const uint4 w = philox4x32_10_ks(make_uint4(site0 + uint32_t(l) * dsite, step_lo, step_hi, blk), keys);
     wav[l][0] = w.x;
     wav[l][1] = w.z;
     hturn[l][0] = (w.y >> 31) + ((w.y >> 30) & 1u);

@@ -56,6 +56,21 @@ class flbm_stats_t(ctypes.Structure):
         }
 
 
+class flbm_lattice_spec(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("dims", ctypes.c_int64 * 3),
+        ("lambda_", ctypes.c_double * 27),
+        ("kBT", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+FLBM_BATCH_MAX_LATTICES = 512
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -95,6 +110,21 @@ def _load():
         "flbm_stats_noalloc": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_double, vp, vp, ctypes.POINTER(flbm_stats_t)]),
         "flbm_last_error": (ctypes.c_char_p, []),
+        "flbm_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(flbm_lattice_spec),
+                                             ctypes.c_int, vp]),
+        "flbm_batch_destroy": (None, [vp]),
+        "flbm_batch_size": (ctypes.c_int, [vp]),
+        "flbm_batch_lattice": (vp, [vp, ctypes.c_int]),
+        "flbm_batch_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "flbm_batch_get_step": (ctypes.c_int64, [vp]),
+        "flbm_batch_set_threads": (ctypes.c_int, [vp, ctypes.c_int]),
+        "flbm_batch_get_threads": (ctypes.c_int, [vp]),
+        "flbm_batch_set_persistent": (ctypes.c_int, [vp, ctypes.c_int]),
+        "flbm_batch_get_persistent": (ctypes.c_int, [vp]),
+        "flbm_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int)]),
+        "flbm_batch_uses_graph": (ctypes.c_int, [vp]),
+        "flbm_batch_sync": (ctypes.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -283,18 +313,103 @@ def flbm_last_error():
     return _lib.flbm_last_error().decode()
 
 
+def _spec(d):
+    """One flbm_lattice_spec from a dict: lattice, dims, lam (Q rates), kBT, rho0, seed."""
+    lattice = int(d["lattice"])
+    lam = _lambda(lattice, d["lam"])
+    s = flbm_lattice_spec()
+    s.lattice = lattice
+    s.reserved = 0
+    dd = [int(x) for x in d["dims"]] + [1] * (3 - len(d["dims"]))
+    for a in range(3):
+        s.dims[a] = dd[a]
+    for v in range(lam.size):
+        s.lambda_[v] = float(lam[v])
+    s.kBT = float(d["kBT"])
+    s.rho0 = float(d.get("rho0", 1.0))
+    s.seed = int(d.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    return s
+
+
+def flbm_batch_create(specs, cuda_stream=None):
+    arr = (flbm_lattice_spec * max(len(specs), 1))(*[_spec(d) for d in specs])
+    b = ctypes.c_void_p()
+    _check(_lib.flbm_batch_create(ctypes.byref(b), arr, len(specs),
+                                  ctypes.c_void_p(cuda_stream) if cuda_stream else None))
+    return b
+
+
+def flbm_batch_destroy(b):
+    _lib.flbm_batch_destroy(b)
+
+
+def flbm_batch_size(b):
+    return int(_lib.flbm_batch_size(b))
+
+
+def flbm_batch_lattice(b, i):
+    h = _lib.flbm_batch_lattice(b, int(i))
+    if not h:
+        raise FlbmError(FLBM_EINVAL, _lib.flbm_last_error().decode())
+    return ctypes.c_void_p(h)
+
+
+def flbm_batch_step(b, n=1):
+    _check(_lib.flbm_batch_step(b, int(n)))
+
+
+def flbm_batch_get_step(b):
+    return int(_lib.flbm_batch_get_step(b))
+
+
+def flbm_batch_set_threads(b, threads):
+    _check(_lib.flbm_batch_set_threads(b, int(threads)))
+
+
+def flbm_batch_get_threads(b):
+    return int(_lib.flbm_batch_get_threads(b))
+
+
+def flbm_batch_set_persistent(b, persistent):
+    _check(_lib.flbm_batch_set_persistent(b, int(bool(persistent))))
+
+
+def flbm_batch_get_persistent(b):
+    return int(_lib.flbm_batch_get_persistent(b))
+
+
+def flbm_batch_autotune(b, trial_steps=10):
+    """Returns (threads, persistent) of the fastest launch shape."""
+    t = ctypes.c_int(-1)
+    p = ctypes.c_int(-1)
+    _check(_lib.flbm_batch_autotune(b, int(trial_steps), ctypes.byref(t), ctypes.byref(p)))
+    return t.value, bool(p.value)
+
+
+def flbm_batch_uses_graph(b):
+    return int(_lib.flbm_batch_uses_graph(b))
+
+
+def flbm_batch_sync(b):
+    _check(_lib.flbm_batch_sync(b))
+
+
 # ---- a thin owner object over the same calls ---------------------------------------------
 class Lattice:
     """Owns one context; methods forward to the C ABI calls of the same name."""
 
     def __init__(self, lattice, dims, lam, kBT, rho0=1.0, seed=0, storage=FLBM_FP32,
-                 cuda_stream=None, dev_buf=None, dev_buf_bytes=0):
+                 cuda_stream=None, dev_buf=None, dev_buf_bytes=0, _borrowed=None):
         self.lattice = int(lattice)
         self.dims = tuple(int(x) for x in dims) + (1,) * (3 - len(dims))
         self.q = Q_OF[self.lattice]
         self.storage = storage
-        self.ctx = flbm_create_ex(lattice, self.dims, lam, kBT, rho0, seed, storage, cuda_stream,
-                                  dev_buf, dev_buf_bytes)
+        self._owned = _borrowed is None
+        if _borrowed is not None:
+            self.ctx = _borrowed
+        else:
+            self.ctx = flbm_create_ex(lattice, self.dims, lam, kBT, rho0, seed, storage, cuda_stream,
+                                      dev_buf, dev_buf_bytes)
 
     @property
     def sites(self):
@@ -350,8 +465,84 @@ class Lattice:
 
     def close(self):
         if self.ctx:
-            flbm_destroy(self.ctx)
+            if self._owned:
+                flbm_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns a batch of independent lattices (flbm_batch_*); ``lattice(i)`` gives a
+    non-owning Lattice view of member i for the read and exchange calls."""
+
+    def __init__(self, specs, cuda_stream=None):
+        self.specs = [dict(d) for d in specs]
+        self.handle = flbm_batch_create(self.specs, cuda_stream)
+        self._views = [None] * len(self.specs)
+
+    def __len__(self):
+        return len(self.specs)
+
+    def lattice(self, i):
+        if not 0 <= int(i) < len(self.specs):
+            flbm_batch_lattice(self.handle, i)  # raises FLBM_EINVAL with the library's message
+        if self._views[i] is None:
+            d = self.specs[i]
+            self._views[i] = Lattice(d["lattice"], d["dims"], None, None,
+                                     _borrowed=flbm_batch_lattice(self.handle, i))
+        return self._views[i]
+
+    def step(self, n=1):
+        flbm_batch_step(self.handle, n)
+
+    @property
+    def step_count(self):
+        return flbm_batch_get_step(self.handle)
+
+    @property
+    def threads(self):
+        return flbm_batch_get_threads(self.handle)
+
+    @threads.setter
+    def threads(self, t):
+        flbm_batch_set_threads(self.handle, t)
+
+    @property
+    def persistent(self):
+        return flbm_batch_get_persistent(self.handle) == 1
+
+    @persistent.setter
+    def persistent(self, p):
+        flbm_batch_set_persistent(self.handle, p)
+
+    def autotune(self, trial_steps=10):
+        return flbm_batch_autotune(self.handle, trial_steps)
+
+    @property
+    def uses_graph(self):
+        return flbm_batch_uses_graph(self.handle) == 1
+
+    def sync(self):
+        flbm_batch_sync(self.handle)
+
+    def close(self):
+        if self.handle:
+            for v in self._views:
+                if v is not None:
+                    v.ctx = None
+            flbm_batch_destroy(self.handle)
+            self.handle = None
 
     def __enter__(self):
         return self

@@ -1,0 +1,232 @@
+"""GPU parity of batched ensembles (flbm_batch_*): every lattice of a batch against the
+FP64 oracle run alone with the same parameters, and against a single context.
+
+Tolerance as for single lattices: max |f_gpu - f_oracle| / (w_i rho0) <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def fl():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_16486_gb300 as fl
+
+    return fl
+
+
+def _w(lattice):
+    if lattice == 0:
+        return np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    return np.array([8 / 27] + [2 / 27] * 6 + [1 / 54] * 12 + [1 / 216] * 8)
+
+
+def _err(a, b, lattice, rho0=1.0):
+    w = _w(lattice).reshape((-1, 1, 1, 1))
+    return float((np.abs(a - b) / (w * rho0)).max())
+
+
+def _lam(lattice, shear, rest=1.0):
+    if lattice == 0:
+        lam = np.full(9, rest)
+        lam[:3] = 1.0
+        lam[[4, 5]] = shear
+    else:
+        lam = np.full(27, rest)
+        lam[:4] = 1.0
+        lam[[7, 8, 9]] = shear
+    return lam
+
+
+def _general(lattice, seed):
+    rng = np.random.default_rng(seed)
+    q, d = (9, 2) if lattice == 0 else (27, 3)
+    lam = np.ones(q)
+    lam[d + 1:] = rng.uniform(0.3, 1.95, q - d - 1)
+    return lam
+
+
+def _specs(general=False):
+    # Even and odd nx for both lattices (paired and unpaired sites), a degenerate box,
+    # kBT over two decades, rho0 != 1, own seeds (one above 2^32).
+    s = [
+        dict(lattice=1, dims=(12, 10, 6), lam=_lam(1, 1.6), kBT=1e-4, rho0=1.0, seed=11),
+        dict(lattice=1, dims=(9, 7, 5), lam=_lam(1, 1.9), kBT=3e-4, rho0=1.0, seed=12),
+        dict(lattice=0, dims=(34, 20, 1), lam=_lam(0, 1.3), kBT=1e-3, rho0=1.0, seed=13),
+        dict(lattice=0, dims=(33, 17, 1), lam=_lam(0, 0.7), kBT=1e-5, rho0=1.3, seed=14),
+        dict(lattice=1, dims=(2, 3, 1), lam=_lam(1, 1.2), kBT=2e-4, rho0=1.0, seed=(1 << 40) + 15),
+        dict(lattice=0, dims=(600, 3, 1), lam=_lam(0, 1.98), kBT=1e-4, rho0=1.0, seed=16),
+    ]
+    if general:
+        s[0]["lam"] = _general(1, 21)
+        s[3]["lam"] = _general(0, 22)
+    return s
+
+
+_U0 = [(0.05, 0.02, 0.0), (-0.03, 0.01, 0.02), (0.04, -0.02, 0.0), (0.0, 0.03, 0.0),
+       (0.01, 0.01, 0.01), (-0.05, 0.0, 0.0)]
+
+
+def _init(batch):
+    f0 = []
+    for i in range(len(batch)):
+        lat = batch.lattice(i)
+        lat.init_uniform(_U0[i], 1e-3, 100 + i)
+        f0.append(lat.populations())
+    return f0
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+@pytest.mark.parametrize("general", [False, True])
+def test_batch_members_match_oracle(fl, oracle_mod, general, persistent):
+    specs = _specs(general)
+    with fl.Batch(specs) as b:
+        b.persistent = persistent
+        f0 = _init(b)
+        b.step(3)
+        b.step(4)  # a second captured shape, then a replay below
+        b.step(3)
+        b.sync()
+        assert b.step_count == 10
+        for i, d in enumerate(specs):
+            lat = b.lattice(i)
+            assert lat.step_count == 10
+            fg = lat.populations()
+            fo = oracle_mod.run(d["lattice"], d["dims"], d["lam"], d["kBT"], d["seed"], f0[i], 0, 10)
+            assert np.abs(fg - f0[i]).max() > 0.0
+            assert _err(fg, fo, d["lattice"], d["rho0"]) <= TOL, i
+
+
+@pytest.mark.parametrize("general", [False, True])
+def test_batch_equals_single_contexts(fl, general):
+    # Each lattice of the batch against a single context with the same parameters and
+    # the same initial state. With general rates the arithmetic is the same code on the
+    # same constants (bitwise); the paper-structure form builds its amplitudes from
+    # sqrt(kBT) on the device, which may move the last bit.
+    specs = _specs(general)
+    with fl.Batch(specs) as b:
+        f0 = _init(b)
+        b.step(25)
+        fb = [b.lattice(i).populations() for i in range(len(specs))]
+    for i, d in enumerate(specs):
+        with fl.Lattice(d["lattice"], d["dims"], d["lam"], d["kBT"], d["rho0"], d["seed"]) as lat:
+            lat.variant = 3
+            lat.set_populations(f0[i])
+            lat.step(25)
+            fs = lat.populations()
+        general_member = general and i in (0, 3)
+        if general_member and d["dims"][0] % 2 == 0:
+            assert np.array_equal(fb[i], fs), i
+        else:
+            assert _err(fb[i], fs, d["lattice"], d["rho0"]) <= 1e-6, i
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+@pytest.mark.parametrize("threads", [64, 128, 256])
+def test_batch_shapes_same_result(fl, threads, persistent):
+    # Every launch shape computes the same update, bit for bit; calls of several sizes
+    # start on both parities.
+    specs = _specs(False)
+    with fl.Batch(specs) as b:
+        _init(b)
+        b.threads = threads
+        b.persistent = persistent
+        assert b.threads == threads and b.persistent == persistent
+        b.step(2)
+        b.step(3)
+        b.step(1)
+        b.step(3)
+        b.sync()
+        assert b.step_count == 9
+        got = [b.lattice(i).populations() for i in range(len(specs))]
+    with fl.Batch(specs) as b:
+        _init(b)
+        b.step(9)
+        ref = [b.lattice(i).populations() for i in range(len(specs))]
+    for g, r in zip(got, ref):
+        assert np.array_equal(g, r)
+
+
+def test_batch_autotune_leaves_state(fl):
+    specs = _specs(False)
+    with fl.Batch(specs) as b:
+        _init(b)
+        b.step(3)
+        before = [b.lattice(i).populations() for i in range(len(specs))]
+        t, p = b.autotune(4)
+        assert t in (64, 128, 256) and b.threads == t and b.persistent == p
+        assert b.step_count == 3
+        after = [b.lattice(i).populations() for i in range(len(specs))]
+        for x, y in zip(before, after):
+            assert np.array_equal(x, y)
+        b.step(5)
+        tuned = [b.lattice(i).populations() for i in range(len(specs))]
+    with fl.Batch(specs) as b:
+        _init(b)
+        b.step(8)
+        ref = [b.lattice(i).populations() for i in range(len(specs))]
+    for x, y in zip(tuned, ref):
+        assert np.array_equal(x, y)
+
+
+def test_batch_member_rules_and_stats(fl, oracle_mod):
+    specs = _specs(False)
+    with fl.Batch(specs) as b:
+        _init(b)
+        lat = b.lattice(0)
+        with pytest.raises(fl.FlbmError) as e:
+            lat.step(1)
+        assert e.value.status == fl.FLBM_ESTATE
+        with pytest.raises(fl.FlbmError) as e:
+            lat.variant = 2
+        assert e.value.status == fl.FLBM_ESTATE
+        fl.flbm_destroy(lat.ctx)  # ignored for a borrowed handle
+        b.step(4)
+        with pytest.raises(fl.FlbmError) as e:
+            lat.init_uniform((0, 0, 0), 0.0, 0)
+        assert e.value.status == fl.FLBM_ESTATE
+        blob = lat.save()
+        b.step(1)
+        with pytest.raises(fl.FlbmError) as e:  # a checkpoint of another step
+            lat.load(blob)
+        assert e.value.status == fl.FLBM_ESTATE
+        # statistics of a member: FP64 reduction against the oracle's
+        for i, d in enumerate(specs):
+            m = b.lattice(i)
+            st = m.stats()
+            so = oracle_mod.stats(d["lattice"], d["dims"], m.populations())
+            assert st["step"] == 5
+            assert abs(st["mass"] - so["mass"]) <= 1e-9 * so["mass"]
+            # per-site products in FP32, sums in FP64: relative to the largest component
+            scale = np.abs(so["uu"]).max()
+            np.testing.assert_allclose(st["uu"], so["uu"], rtol=0, atol=1e-6 * scale)
+        with pytest.raises(fl.FlbmError):
+            b.lattice(len(specs))
+
+
+def test_batch_invalid_specs(fl):
+    good = _specs(False)[:2]
+    bad = [dict(good[0]), dict(good[1])]
+    bad[1]["dims"] = (4, 4, 4)
+    bad[1]["lattice"] = 0  # D2Q9 with nz = 4
+    bad[1]["lam"] = np.full(9, 1.5)
+    with pytest.raises(fl.FlbmError) as e:
+        fl.Batch(bad)
+    assert e.value.status == fl.FLBM_EINVAL and "specs[1]" in str(e.value)
+    with pytest.raises(fl.FlbmError):
+        fl.flbm_batch_create([])
+    with fl.Batch(good) as b:
+        with pytest.raises(fl.FlbmError):
+            b.threads = 96
+        with pytest.raises(fl.FlbmError):
+            b.step(-1)
+        b.step(0)
+        assert b.step_count == 0
+        assert fl.flbm_batch_uses_graph(b.handle) in (0, 1)
