@@ -16,10 +16,6 @@
 
 namespace flbm {
 
-struct Normals4 {
-  float z0, z1, z2, z3;
-};
-
 __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int round = 0; round < 10; ++round) {
@@ -38,25 +34,6 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint32_t k0, uint32_t 
 // (m + 0.5) 2^-23 has 24 significant bits, so it is exact in FP32.
 __device__ __forceinline__ float uniform01(uint32_t w) {
   return fmaf(static_cast<float>(w >> 9), 0x1p-23f, 0x1p-24f);
-}
-
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &za, float &zb) {
-  const float ua = uniform01(wa);
-  const float ub = uniform01(wb);
-  const float r = sqrtf(-2.0f * logf(ua));
-  float s, c;
-  sincospif(2.0f * ub, &s, &c);
-  za = r * c;
-  zb = r * s;
-}
-
-__device__ __forceinline__ Normals4 normals4(uint32_t site, uint32_t step_lo, uint32_t step_hi,
-                                             uint32_t tag_blk, uint32_t k0, uint32_t k1) {
-  const uint4 w = philox4x32_10(make_uint4(site, step_lo, step_hi, tag_blk), k0, k1);
-  Normals4 n;
-  box_muller(w.x, w.y, n.z0, n.z1);
-  box_muller(w.z, w.w, n.z2, n.z3);
-  return n;
 }
 
 // Round keys of Philox4x32-10: key + r (W0, W1). KeyTable reads them precomputed (kernel
@@ -85,50 +62,23 @@ __device__ __forceinline__ uint4 philox4x32_10_ks(uint4 ctr, const K &keys) {
   return ctr;
 }
 
-// Box-Muller with the angle reduced exactly in integers. For u_b = (m + 1/2) 2^-23,
-// m = w_b >> 9, the nearest half turn is h = round(2 u_b) (0, 1 or 2, from the top two
-// bits of w_b) and 2 pi u_b - h pi = (m - h 2^22 + 1/2) pi 2^-22, a number in
-// [-pi/2, pi/2] formed with one rounding. sin and cos of it are their Taylor series
-// (to r^13 and r^14; truncation below 7e-10), and cos(2 pi u_b) = (-1)^h cos r,
-// sin(2 pi u_b) = (-1)^h sin r. Checked against the FP64 definition over all 2^23 angle
-// codes: |error| < 2e-7.
+// Box-Muller, angle: cos and sin of 2 pi u_b depend only on u_b mod 1, and the word read
+// as a signed integer gives exactly that residue in [-1/2, 1/2): (int)w_b >> 9 is m - 2^23
+// when the top bit of w_b is set, m otherwise. So theta = ((int)w_b >> 9 + 1/2) 2 pi 2^-23
+// lies in (-pi, pi) (one FMA on an exactly converted integer) and cos / sin come from the
+// hardware approximations (__sincosf; absolute error about 4e-7 on [-pi, pi]), which cost
+// two instructions instead of a polynomial.
 //
 // The radius: u_a = (2 m_a + 1) 2^-24 with y = 2 m_a + 1 an odd integer below 2^24, so
 // -2 ln u_a = -2 (ln y - 24 ln 2). y converts to FP32 exactly; the argument reduction
 // of Cody & Waite (Software Manual for the Elementary Functions, 1980) writes y = 2^k x
 // with x in [sqrt(1/2), sqrt(2)), and ln x = 2 atanh(s) = 2 (s + s^3/3 + ... + s^9/9),
 // s = (x - 1)/(x + 1), |s| < 0.172 (truncation below 1e-9 relative). x - 1 is exact,
-// so the result keeps its relative accuracy as u_a -> 1, where r -> 0. Checked against
-// the FP64 definition over all 2^23 codes: relative error of -2 ln u_a below 3e-7.
-constexpr float kAngleScale = 0x1p-22f * 3.14159265358979323846f;
-constexpr float kAngleOffset = 0x1p-23f * 3.14159265358979323846f;
-
-
-template <typename T>
-__device__ __forceinline__ void sincos_taylor(T r, T &s, T &c) {
-  const T r2 = vmul(r, r);
-  T p = vfma(r2, splat<T>(1.0f / 6227020800.0f), splat<T>(-1.0f / 39916800.0f));
-  p = vfma(p, r2, splat<T>(1.0f / 362880.0f));
-  p = vfma(p, r2, splat<T>(-1.0f / 5040.0f));
-  p = vfma(p, r2, splat<T>(1.0f / 120.0f));
-  p = vfma(p, r2, splat<T>(-1.0f / 6.0f));
-  s = vfma(vmul(r2, r), p, r);
-  T q = vfma(r2, splat<T>(-1.0f / 87178291200.0f), splat<T>(1.0f / 479001600.0f));
-  q = vfma(q, r2, splat<T>(-1.0f / 3628800.0f));
-  q = vfma(q, r2, splat<T>(1.0f / 40320.0f));
-  q = vfma(q, r2, splat<T>(-1.0f / 720.0f));
-  q = vfma(q, r2, splat<T>(1.0f / 24.0f));
-  q = vfma(q, r2, splat<T>(-0.5f));
-  c = vfma(q, r2, splat<T>(1.0f));
-}
-
-// (cos, sin) of h pi + r from (cos r, sin r), times rad.
-__device__ __forceinline__ void bm_finish(float s, float c, uint32_t half, float rad, float &za,
-                                          float &zb) {
-  const float rr = __int_as_float(__float_as_int(rad) ^ ((half & 1u) << 31));  // (-1)^h rad
-  za = rr * c;
-  zb = rr * s;
-}
+// so the result keeps its relative accuracy as u_a -> 1, where r -> 0 (a hardware
+// logarithm has an absolute error there that exceeds the value). Checked against the FP64
+// definition over all 2^23 codes: relative error of -2 ln u_a below 3e-7.
+constexpr float kAngleScale = 0x1p-23f * 6.28318530717958647692f;  // 2 pi 2^-23
+constexpr float kAngleOffset = 0x1p-23f * 3.14159265358979323846f;  // pi 2^-23
 
 // Four normals of Philox block `blk` for each lane's site (lane l: site0 + l * dsite),
 // each multiplied by `scale` of its lane (the caller's sqrt(rho)).
@@ -137,18 +87,15 @@ __device__ __forceinline__ void normals4_scaled(uint32_t site0, uint32_t step_lo
                                                 uint32_t blk, const K &keys, T scale, T (&z)[4],
                                                 uint32_t dsite = 1) {
   constexpr int L = Lanes<T>::n;
-  float rad[L][2], ang_l[L][2];
-  uint32_t hturn[L][2];
+  float ang[L][2];
   uint32_t wav[L][2];
 #pragma unroll
   for (int l = 0; l < L; ++l) {
     const uint4 w = philox4x32_10_ks(make_uint4(site0 + uint32_t(l) * dsite, step_lo, step_hi, blk), keys);
     wav[l][0] = w.x;
     wav[l][1] = w.z;
-    hturn[l][0] = (w.y >> 31) + ((w.y >> 30) & 1u);
-    ang_l[l][0] = fmaf((float)((int)(w.y >> 9) - (int)(hturn[l][0] << 22)), kAngleScale, kAngleOffset);
-    hturn[l][1] = (w.w >> 31) + ((w.w >> 30) & 1u);
-    ang_l[l][1] = fmaf((float)((int)(w.w >> 9) - (int)(hturn[l][1] << 22)), kAngleScale, kAngleOffset);
+    ang[l][0] = fmaf((float)((int)w.y >> 9), kAngleScale, kAngleOffset);
+    ang[l][1] = fmaf((float)((int)w.w >> 9), kAngleScale, kAngleOffset);
   }
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
@@ -176,26 +123,19 @@ __device__ __forceinline__ void normals4_scaled(uint32_t site0, uint32_t step_lo
     P = vfma(P, s2, splat<T>(-4.0f / 3.0f));
     P = vfma(P, s2, splat<T>(-4.0f));
     const T a = vfma(kf, splat<T>(-1.38629436f), vmul(sx, P));  // -2 ln u_a (kf = k - 24)
+    T rad, c, sn;
 #pragma unroll
     for (int l = 0; l < L; ++l) {
       const float al = lane(a, l);
-      rad[l][p] = al * rsqrtf(al) * lane(scale, l);
+      set_lane(rad, l, al * rsqrtf(al));
+      float sl, cl;
+      __sincosf(ang[l][p], &sl, &cl);
+      set_lane(sn, l, sl);
+      set_lane(c, l, cl);
     }
-  }
-
-#pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    T ang, s, c;
-#pragma unroll
-    for (int l = 0; l < L; ++l) set_lane(ang, l, ang_l[l][p]);
-    sincos_taylor(ang, s, c);
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-      float za, zb;
-      bm_finish(lane(s, l), lane(c, l), hturn[l][p], rad[l][p], za, zb);
-      set_lane(z[2 * p], l, za);
-      set_lane(z[2 * p + 1], l, zb);
-    }
+    rad = vmul(rad, scale);
+    z[2 * p] = vmul(rad, c);
+    z[2 * p + 1] = vmul(rad, sn);
   }
 }
 
