@@ -206,8 +206,9 @@ int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storage, int pari
  * sites per thread, 3 = two sites per thread with the noise generated in a rolled loop
  * (smaller code), 4 = a persistent kernel that prefetches each row's populations into
  * shared memory with bulk asynchronous copies (needs nx even, nx <= 512 and a
- * population row a multiple of 16 bytes; else it falls back to 2). Variants 2-4 fall
- * back to 1 when nx is odd. The environment variable FLBM_STEP_VARIANT, read by
+ * population row a multiple of 16 bytes; else it falls back to 2), 5 and 6 = 2 and 3
+ * compiled for five resident blocks per SM (at most 102 registers, more warps to hide
+ * latency; for D2Q9 they are 2 and 3). Variants 2-6 fall back to 1 when nx is odd. The environment variable FLBM_STEP_VARIANT, read by
  * flbm_create, sets the initial choice.
  * flbm_autotune times every applicable variant over trial_steps steps on a copy of the
  * current state (restored afterwards: populations and step count are unchanged), keeps

@@ -646,8 +646,10 @@ int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
       st = fail(FLBM_ECUDA, "autotune set-up: %s", cudaGetErrorString(cudaGetLastError()));
       break;
     }
-    const int candidates[4] = {kStepOneSite, kStepPair, kStepPairRolled, kStepPipelined};
+    const int candidates[6] = {kStepOneSite, kStepPair, kStepPairRolled, kStepPipelined, kStepPairOcc,
+                               kStepPairRolledOcc};
     for (int v : candidates) {
+      if ((v == kStepPairOcc || v == kStepPairRolledOcc) && c->D != 3) continue;  // same as 2 and 3
       if (v != kStepOneSite && c->dims[0] % 2 != 0) continue;
       if (v == kStepPipelined && !pipe_applicable(c->D, c->storage, int(c->dims[0]))) continue;
       c->variant = v;

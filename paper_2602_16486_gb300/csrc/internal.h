@@ -78,7 +78,9 @@ enum StepVariant {
   kStepPair = 2,
   kStepPairRolled = 3,
   kStepPipelined = 4,
-  kStepVariantMax = 4
+  kStepPairOcc = 5,        // as 2, register cap for five blocks per SM (D3Q27)
+  kStepPairRolledOcc = 6,  // as 3, register cap for five blocks per SM (D3Q27)
+  kStepVariantMax = 6
 };
 bool pipe_applicable(int D, int storage, int nx);
 cudaError_t launch_step(int D, int storage, int variant, int parity, bool noise, bool shear,

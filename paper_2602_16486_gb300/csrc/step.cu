@@ -22,8 +22,8 @@
 //   step2_kernel - two sites per thread (x0 = 2 t, x0 + 1; nx even): every floating-
 //                  point step runs as packed FP32x2, population pairs move as one 8-byte
 //                  (FP32) or 4-byte (16-bit) access, per-population address offsets are
-//                  block-uniform; capped at 128 registers (4 blocks of 4 warps per SM);
-//                  the noise loop is unrolled or rolled (smaller code).
+//                  block-uniform; capped at 128 registers (4 blocks of 4 warps per SM)
+//                  or 102 (5 blocks); the noise loop is unrolled or rolled (smaller code).
 // Warps touch contiguous runs of every population, so all accesses are coalesced (odd
 // steps are shifted by one element, which costs no extra DRAM traffic).
 #include <cuda_runtime.h>
@@ -52,8 +52,8 @@ __global__ void __launch_bounds__(kStepBlock) step_kernel(const StepArgs a) {
   store_streamed<D, S, PARITY>(f, a.plane, nb, F);
 }
 
-template <int D, typename S, int PARITY, bool NOISE, bool ROLLED, bool SHEAR>
-__global__ void __launch_bounds__(kStepBlock, 4) step2_kernel(const StepArgs a) {
+template <int D, typename S, int PARITY, bool NOISE, bool ROLLED, bool SHEAR, int MINB>
+__global__ void __launch_bounds__(kStepBlock, MINB) step2_kernel(const StepArgs a) {
   const int x0 = 2 * (blockIdx.x * kStepBlock + threadIdx.x);
   if (x0 >= a.nx) return;
   const Addr2 ad = addr2(x0, blockIdx.y, blockIdx.z, a.nx, a.ny, a.nz);
@@ -74,12 +74,20 @@ constexpr int storage_code() {
 template <int D, typename S, int PARITY, bool NOISE, bool SHEAR>
 cudaError_t launch_kernel(int variant, const StepArgs &a, cudaStream_t s) {
   const dim3 block(kStepBlock);
-  if (variant == kStepPair || variant == kStepPairRolled) {
+  if (variant != kStepOneSite) {
+    // Register caps: 128 (four blocks of 128 threads per SM) or, for D3Q27, 102 (five
+    // blocks: more warps to hide latency, at the risk of spills). D2Q9 needs fewer than
+    // 102 registers either way, so its variants 5 and 6 are 2 and 3.
+    constexpr int kOcc = D == 3 ? 5 : 4;
     const dim3 grid((a.nx / 2 + kStepBlock - 1) / kStepBlock, a.ny, a.nz);
     if (variant == kStepPairRolled)
-      step2_kernel<D, S, PARITY, NOISE, true, SHEAR><<<grid, block, 0, s>>>(a);
+      step2_kernel<D, S, PARITY, NOISE, true, SHEAR, 4><<<grid, block, 0, s>>>(a);
+    else if (variant == kStepPairOcc)
+      step2_kernel<D, S, PARITY, NOISE, false, SHEAR, kOcc><<<grid, block, 0, s>>>(a);
+    else if (variant == kStepPairRolledOcc)
+      step2_kernel<D, S, PARITY, NOISE, true, SHEAR, kOcc><<<grid, block, 0, s>>>(a);
     else
-      step2_kernel<D, S, PARITY, NOISE, false, SHEAR><<<grid, block, 0, s>>>(a);
+      step2_kernel<D, S, PARITY, NOISE, false, SHEAR, 4><<<grid, block, 0, s>>>(a);
   } else {
     const dim3 grid((a.nx + kStepBlock - 1) / kStepBlock, a.ny, a.nz);
     step_kernel<D, S, PARITY, NOISE, SHEAR><<<grid, block, 0, s>>>(a);

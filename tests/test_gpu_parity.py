@@ -74,7 +74,7 @@ def test_d2q9_64x64_fp64_config_parity(fl, oracle_mod):
     assert _err(fg, fo, 0) <= TOL
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
 def test_d3q27_drift_perturbed_ragged_box(fl, oracle_mod, variant):
     # The headline workload's physics (drift (0.05, 0.02, 0), 1e-3 density perturbation,
     # kBT = 1e-4, shear omega = 1.6) on a box spanning three x-blocks (one site per thread)
@@ -162,7 +162,7 @@ def test_autotune_leaves_the_state_unchanged(fl):
         lat.step(3)
         before = lat.populations()
         chosen = lat.autotune(4)
-        assert chosen in (1, 2, 3, 4) and lat.variant == chosen
+        assert chosen in (1, 2, 3, 4, 5, 6) and lat.variant == chosen
         assert lat.step_count == 3
         assert np.array_equal(lat.populations(), before)
         lat.variant = 1
@@ -291,7 +291,7 @@ def test_reduced_precision_pipelined_matches_pair_kernel(fl, storage):
     # or not); with 16-bit storage their stored results must agree bit for bit.
     lam = _lam(1, 1.6)
     out = []
-    for variant in (2, 3, 4):
+    for variant in (2, 3, 4, 5, 6):
         with fl.Lattice(1, (64, 9, 7), lam, 1e-4, 1.0, 5, storage) as lat:
             lat.variant = variant
             assert lat.variant == variant
