@@ -9,7 +9,9 @@ u0 = (0.05, 0.02, 0), kBT = 1e-4, shear rate omega = 1.6 (Lambda_7-9), all other
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0). N > 1 runs N independent replicas (one lattice per
-GPU, weak scaling, no data exchange) launched by torch.distributed.run.
+GPU, weak scaling, no data exchange) launched by torch.distributed.run. At N = 1 the
+line also carries the same workload with BF16 and FP16 deviation storage
+("storage_widths") and the 256-lattice batched ensemble ("batched_ensemble").
 `--impl reference` times the FP64 CPU oracle on this host's cores on a bounded
 sample of the same workload.
 """
@@ -72,13 +74,18 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# Sources the single-lattice step kernels are compiled from (a change to any of them
+# invalidates recorded DRAM counters).
+STEP_SOURCES = ("step.cu", "step_pipe.cu", "async.cuh", "cm.cuh", "collide.cuh", "philox.cuh", "lattice.cuh",
+                "vec.cuh", "internal.h")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2602_16486_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode() + fh.read())
+    for name in STEP_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -318,6 +325,9 @@ def run_ours(args):
         "clocks": clocks.summary(),
         "nonfinite_sites_in_samples": int(nonfinite),
     }
+    if world == 1 and not args.no_extras:
+        line["storage_widths"] = storage_widths(fl, torch, stream, dims, peaks["hbm_gbs"])
+        line["batched_ensemble"] = batched_ensemble(fl, torch, peaks["hbm_gbs"])
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     if world > 1:
@@ -325,6 +335,104 @@ def run_ours(args):
 
         dist.destroy_process_group()
     return line
+
+
+# ---- the two other systems forms: 16-bit storage and batched ensembles -------------------
+def draw_ensemble(n=256, seed=0):
+    """The batched-ensemble workload: n lattices drawn from `seed`: D2Q9 or D3Q27 with
+    probability 1/2, side log-uniform in [32, 256] (D2Q9) or [16, 64] (D3Q27), kBT
+    log-uniform in [1e-5, 1e-3], shear relaxation time tau uniform in [0.51, 2.0]
+    (Lambda_shear = 1/tau, every other non-conserved mode 1), seed 1000 + j."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for j in range(n):
+        d3 = rng.random() < 0.5
+        lo, hi = (16, 64) if d3 else (32, 256)
+        side = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        kbt = float(np.exp(rng.uniform(np.log(1e-5), np.log(1e-3))))
+        tau = float(rng.uniform(0.51, 2.0))
+        lam = np.ones(27 if d3 else 9)
+        lam[[7, 8, 9] if d3 else [4, 5]] = 1.0 / tau
+        specs.append(dict(lattice=1 if d3 else 0, dims=(side, side, side if d3 else 1), lam=lam, kBT=kbt,
+                          rho0=1.0, seed=1000 + j))
+    return specs
+
+
+def _event_time(torch, stream, fn, n):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn(n)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / n
+
+
+def storage_widths(fl, torch, stream, dims, peak):
+    """GLUPS of the same workload with BF16 and FP16 deviation storage (FP32 arithmetic)."""
+    out = {}
+    sites = dims[0] * dims[1] * dims[2]
+    for storage, name in ((fl.FLBM_BF16, "bf16"), (fl.FLBM_FP16, "fp16")):
+        with fl.Lattice(fl.FLBM_D3Q27, dims, lam_d3q27(), KBT, 1.0, SEED, storage,
+                        cuda_stream=stream.cuda_stream) as lat:
+            lat.init_uniform(U0, AMP, SEED)
+            variant = lat.autotune(10)
+            lat.step(6)
+            ms = _event_time(torch, stream, lat.step, 200)
+            gbs = 27 * 2 * 2 * sites / (ms * 1e-3) / 1e9
+            out[name] = {"value": round(sites / (ms * 1e-3) / 1e9, 3), "unit": UNIT, "ms_per_step": round(ms, 5),
+                         "step_variant": variant, "achieved_gbs": round(gbs, 1),
+                         "frac_of_hbm": round(gbs / peak, 4), "bytes_per_site": 108}
+    return out
+
+
+def batched_ensemble(fl, torch, peak, steps=200):
+    """The batched-ensemble workload in one batch (per-step graph-captured launches or one
+    persistent launch, as the autotuner picks) against the same lattices stepped one
+    context at a time."""
+    specs = draw_ensemble()
+    sites = sum(int(np.prod(d["dims"])) for d in specs)
+    nbytes = sum(int(np.prod(d["dims"])) * (27 if d["lattice"] else 9) * 8 for d in specs)
+    with fl.Batch(specs) as b:
+        for i in range(len(specs)):
+            b.lattice(i).init_uniform((0.0, 0.0, 0.0), 0.0, 0)
+        threads, form = b.autotune(10)
+        b.step(4)
+        b.step(steps)  # capture of the timed call's graph
+        b.sync()
+        t = time.perf_counter()
+        b.step(steps)
+        b.sync()
+        ms = (time.perf_counter() - t) * 1e3 / steps
+        graph = b.uses_graph
+    lats = [fl.Lattice(d["lattice"], d["dims"], d["lam"], d["kBT"], d["rho0"], d["seed"]) for d in specs]
+    try:
+        for lat in lats:
+            lat.init_uniform((0.0, 0.0, 0.0), 0.0, 0)
+            lat.step(2)
+        for lat in lats:
+            lat.sync()
+        n = 20
+        t = time.perf_counter()
+        for _ in range(n):
+            for lat in lats:
+                lat.step(1)
+        for lat in lats:
+            lat.sync()
+        ms_loop = (time.perf_counter() - t) * 1e3 / n
+    finally:
+        for lat in lats:
+            lat.close()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"workload": "256 lattices drawn from seed 0 (D2Q9 32^2..256^2 / D3Q27 16^3..64^3, kBT 1e-5..1e-3, "
+                        "tau 0.51..2.0, seeds 1000+j), FP32",
+            "lattices": len(specs), "sites": sites, "value": round(sites / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
+            "ms_per_step": round(ms, 5), "achieved_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4),
+            "threads": threads, "form": ["per-step launches", "persistent launch", "per-step launches, 5 blocks/SM",
+                                         "per-step launches, rolled noise loop"][form], "graph": graph,
+            "single_context_loop_ms_per_step": round(ms_loop, 5),
+            "speedup_vs_single_context_loop": round(ms_loop / ms, 3),
+            "timing": "wall clock around synchronised calls (own stream)"}
 
 
 # ---- the oracle on the host cores ---------------------------------------------------------
@@ -421,7 +529,9 @@ def main(argv=None):
                    help="box for profiling runs (default 256,256,256: the workload)")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     p.add_argument("--variant", type=int, default=0,
-                   help="step-kernel variant (1-4); default 0 = autotune")
+                   help="step-kernel variant (1-6); default 0 = autotune")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the 16-bit storage and batched-ensemble measurements")
     args = p.parse_args(argv)
     if args.warmup < 3:
         p.error("--warmup must be >= 3")

@@ -277,35 +277,37 @@ int flbm_batch_size(const flbm_batch *b);
 flbm_ctx *flbm_batch_lattice(flbm_batch *b, int i);
 
 /*
- * flbm_batch_step - enqueue n >= 0 steps of every lattice. Never synchronises. Two
- * launch forms compute the same update (bitwise):
- *   per-step (default): one plain launch per step over every tile of every lattice
+ * flbm_batch_step - enqueue n >= 0 steps of every lattice. Never synchronises. Every
+ * launch form (see flbm_batch_set_shape) computes the same update (bitwise):
+ *   per-step forms: per step one plain launch per lattice type over all of its tiles
  *     (block = tile), then a one-thread update of the device step counter;
- *   persistent: one cooperative launch of co-resident blocks that walk (step, tile)
+ *   persistent form: one cooperative launch of co-resident blocks that walk (step, tile)
  *     items in order; a tile of lattice L waits (bounded) for all of L's tiles of the
  *     step before, through per-lattice completion counters, instead of a grid barrier.
- * Either way the n steps are captured once into a CUDA graph per (n, form, parity of the
- * starting step) and replayed, where the stream allows capture. A bounded wait that
- * gives up ends the persistent launch and makes the next flbm_batch_sync return
- * FLBM_ETIMEOUT (the state is then not valid).
+ * The n steps are captured once into a CUDA graph per (n, starting parity) and shape and
+ * replayed, where the stream allows capture. A bounded wait that gives up ends the
+ * persistent launch and makes the next flbm_batch_sync return FLBM_ETIMEOUT (the state
+ * is then not valid).
  */
 int flbm_batch_step(flbm_batch *b, int64_t n);
 int64_t flbm_batch_get_step(const flbm_batch *b);
 
 /*
  * Launch shape: threads per block (64, 128 or 256; every block takes tiles of
- * 2 * threads sites; 0 restores the default, 128) and the launch form (persistent 1,
- * per-step 0). flbm_batch_autotune times every (form, threads) pair over trial_steps
- * steps (rounded up to even) on a copy of the state (restored afterwards, step count
- * unchanged), keeps the fastest and returns it in *threads and *persistent (either may
- * be NULL). Needs one extra copy of all populations in device memory while it runs.
- * Synchronises.
+ * 2 * threads sites; 0 = the default, 128) and the form:
+ *   0 per-step launches, up to 128 registers, D3Q27 noise loop unrolled (default);
+ *   1 persistent cooperative launch (rolled noise loop, both lattice types in one kernel);
+ *   2 per-step launches compiled for five resident blocks per SM (up to 102 registers;
+ *     threads <= 128);
+ *   3 per-step launches, up to 128 registers, D3Q27 noise loop rolled (smaller code).
+ * flbm_batch_autotune times every (form, threads) pair over trial_steps steps (rounded
+ * up to even) on a copy of the state (restored afterwards, step count unchanged), keeps
+ * the fastest and returns it in *threads and *form (either may be NULL). Needs one extra
+ * copy of all populations in device memory while it runs. Synchronises.
  */
-int flbm_batch_set_threads(flbm_batch *b, int threads);
-int flbm_batch_get_threads(const flbm_batch *b);
-int flbm_batch_set_persistent(flbm_batch *b, int persistent);
-int flbm_batch_get_persistent(const flbm_batch *b);
-int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads, int *persistent);
+int flbm_batch_set_shape(flbm_batch *b, int threads, int form);
+int flbm_batch_get_shape(const flbm_batch *b, int *threads, int *form);
+int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads, int *form);
 
 /* 1 when the last flbm_batch_step replayed a captured graph, 0 when it launched
  * directly (capture unavailable on this stream or runtime), -1 for a NULL handle. */

@@ -719,7 +719,7 @@ struct flbm_batch {
   BatchGroup g3{}, g2{};   // the two lattice types' table entries and tiles
   bool shear = true;       // every lattice follows the paper's rate structure
   int threads = 128;       // block size; tiles hold 2 * threads sites
-  bool persistent = false;  // one cooperative launch per call (else one launch per step)
+  int form = kBatchStep;    // enum BatchForm: per-step launches or one persistent launch
   int grid = 0;            // co-resident blocks (cooperative launch)
   int tiles_for = 0;       // block size the tiling was built for
   int ntiles = 0;
@@ -851,8 +851,8 @@ int batch_enqueue(flbm_batch *b, int64_t n) {
   b->args->done = b->d_done;
   b->args->exits = b->d_exits;
   b->args->status = b->d_status;
-  if (!b->persistent) {
-    FLBM_CUDA(launch_batch_steps(b->shear, int(b->step & 1), *b->args, b->g3, b->g2, int(n), b->threads,
+  if (b->form != kBatchPersistent) {
+    FLBM_CUDA(launch_batch_steps(b->form, b->shear, int(b->step & 1), *b->args, b->g3, b->g2, int(n), b->threads,
                                  b->stream));
     return FLBM_OK;
   }
@@ -866,7 +866,7 @@ int batch_enqueue(flbm_batch *b, int64_t n) {
 // unavailable.
 cudaGraphExec_t batch_graph(flbm_batch *b, int64_t n) {
   if (!b->graphs_ok) return nullptr;
-  const int64_t key = n * 4 + (b->persistent ? 2 : int64_t(b->step & 1));
+  const int64_t key = n * 2 + (b->form == kBatchPersistent ? 0 : int64_t(b->step & 1));
   auto it = b->graphs.find(key);
   if (it != b->graphs.end()) return it->second;
   if (b->graphs.size() >= 16) batch_drop_graphs(b);
@@ -1032,26 +1032,26 @@ int flbm_batch_step(flbm_batch *b, int64_t n) {
 
 int64_t flbm_batch_get_step(const flbm_batch *b) { return b ? b->step : -1; }
 
-int flbm_batch_set_threads(flbm_batch *b, int threads) {
+int flbm_batch_set_shape(flbm_batch *b, int threads, int form) {
   if (!b) return fail(FLBM_EINVAL, "batch is NULL");
   if (threads == 0) threads = kBatchDefaultThreads;
   if (threads != 64 && threads != 128 && threads != 256)
     return fail(FLBM_EINVAL, "threads = %d must be 64, 128 or 256 (or 0)", threads);
-  if (threads != b->threads) batch_drop_graphs(b);
+  if (form < 0 || form > kBatchFormMax) return fail(FLBM_EINVAL, "form = %d is not one of 0..%d", form, int(kBatchFormMax));
+  if (form == kBatchStepOcc && threads > 128)
+    return fail(FLBM_EINVAL, "form 2 (five blocks per SM) takes at most 128 threads per block");
+  if (threads != b->threads || form != b->form) batch_drop_graphs(b);
   b->threads = threads;
+  b->form = form;
   return FLBM_OK;
 }
 
-int flbm_batch_set_persistent(flbm_batch *b, int persistent) {
+int flbm_batch_get_shape(const flbm_batch *b, int *threads, int *form) {
   if (!b) return fail(FLBM_EINVAL, "batch is NULL");
-  if (persistent != 0 && persistent != 1) return fail(FLBM_EINVAL, "persistent must be 0 or 1");
-  b->persistent = persistent == 1;
+  if (threads) *threads = b->threads;
+  if (form) *form = b->form;
   return FLBM_OK;
 }
-
-int flbm_batch_get_persistent(const flbm_batch *b) { return b ? (b->persistent ? 1 : 0) : -1; }
-
-int flbm_batch_get_threads(const flbm_batch *b) { return b ? b->threads : -1; }
 
 int flbm_batch_uses_graph(const flbm_batch *b) { return b ? (b->last_graph ? 1 : 0) : -1; }
 
@@ -1068,7 +1068,7 @@ int flbm_batch_sync(flbm_batch *b) {
   return FLBM_OK;
 }
 
-int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads_out, int *persistent_out) {
+int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads_out, int *form_out) {
   if (!b) return fail(FLBM_EINVAL, "batch is NULL");
   if (trial_steps < 2) return fail(FLBM_EINVAL, "trial_steps must be >= 2");
   DeviceGuard g(b->device);
@@ -1079,25 +1079,25 @@ int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads_out, int *p
   }
   const int64_t step0 = b->step;
   const long long step0_dev = (long long)step0;
-  const int saved_t = b->threads;
-  const bool saved_p = b->persistent;
-  int best_t = saved_t, st = FLBM_OK;
-  bool best_p = saved_p;
+  const int saved_t = b->threads, saved_f = b->form;
+  int best_t = saved_t, best_f = saved_f, st = FLBM_OK;
   float best = 1e30f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // warm-up and capture of the timed shape (an even count keeps the start parity of the
+  // timed call, so that it replays the captured graph)
+  const int64_t nt = trial_steps + (trial_steps & 1);
   do {
     if (cudaMemcpyAsync(backup, b->pool, b->pool_bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
       st = fail(FLBM_ECUDA, "autotune set-up: %s", cudaGetErrorString(cudaGetLastError()));
       break;
     }
-    for (int p = 0; p < 2 && st == FLBM_OK; ++p) {
+    for (int f = 0; f <= kBatchFormMax && st == FLBM_OK; ++f) {
       for (int t : {64, 128, 256}) {
+        if (f == kBatchStepOcc && t > 128) continue;
         b->threads = t;
-        b->persistent = p == 1;
-        // warm-up and capture of the timed shape (an even count keeps the start parity
-        // of the timed call, so that it replays the captured graph)
-        const int64_t nt = trial_steps + (trial_steps & 1);
+        b->form = f;
+        batch_drop_graphs(b);
         if ((st = flbm_batch_step(b, 2)) != FLBM_OK) break;
         if ((st = flbm_batch_step(b, nt)) != FLBM_OK) break;
         cudaEventRecord(e0, b->stream);
@@ -1109,7 +1109,7 @@ int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads_out, int *p
         if (ms < best) {
           best = ms;
           best_t = t;
-          best_p = p == 1;
+          best_f = f;
         }
         b->step = step0;
         for (flbm_ctx *c : b->members) c->step = step0;
@@ -1130,16 +1130,16 @@ int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads_out, int *p
   cudaFree(backup);
   b->step = step0;
   for (flbm_ctx *c : b->members) c->step = step0;
+  batch_drop_graphs(b);
   if (st != FLBM_OK) {
     b->threads = saved_t;
-    b->persistent = saved_p;
+    b->form = saved_f;
     return st;
   }
-  if (best_t != b->threads) batch_drop_graphs(b);
   b->threads = best_t;
-  b->persistent = best_p;
+  b->form = best_f;
   if (threads_out) *threads_out = best_t;
-  if (persistent_out) *persistent_out = best_p ? 1 : 0;
+  if (form_out) *form_out = best_f;
   return FLBM_OK;
 }
 

@@ -42,16 +42,16 @@ constexpr uint32_t kWaitSpin = 1u << 22;  // polls of about a microsecond each
 // The collision with lattice L's parameters: its three shear-structure numbers (SHEAR:
 // per-mode factors are compile-time constants) or its per-mode arrays; round keys are
 // formed from its key.
-template <int D, bool SHEAR>
+template <int D, bool SHEAR, bool ROLLED>
 __device__ __forceinline__ void collide_lattice(float2 (&F)[3][3][3], const BatchLattice &L, const float *rates,
                                                 uint32_t s0, uint32_t dsite, uint32_t step_lo, uint32_t step_hi) {
   const KeyBase keys{L.key0, L.key1};
   if (SHEAR)
-    collide_rates<D, true, float2, true, true>(F, L.rho0, ShearRates<D>{L.sqrt_kbt, L.om_shear, L.phc_shear}, s0,
-                                               step_lo, step_hi, keys, dsite);
+    collide_rates<D, true, float2, ROLLED, true>(F, L.rho0, ShearRates<D>{L.sqrt_kbt, L.om_shear, L.phc_shear},
+                                                 s0, step_lo, step_hi, keys, dsite);
   else
-    collide_rates<D, true, float2, true, false>(F, L.rho0, ArrayRates{rates, rates + 27}, s0, step_lo, step_hi,
-                                                keys, dsite);
+    collide_rates<D, true, float2, ROLLED, false>(F, L.rho0, ArrayRates{rates, rates + 27}, s0, step_lo, step_hi,
+                                                  keys, dsite);
 }
 
 // Coordinates of site s of lattice L (32-bit arithmetic: every site index is < 2^32).
@@ -68,7 +68,7 @@ __device__ __forceinline__ void site_xyz(const BatchLattice &L, uint32_t s, int 
 // Otherwise (nx odd) lane l takes site first + t + l * blockDim.x, so that every access
 // of a warp is a contiguous run. Either way the neighbour addresses are recomputed at
 // the store rather than kept live across the collision (register pressure).
-template <int D, int PARITY, bool SHEAR, bool PAIR>
+template <int D, int PARITY, bool SHEAR, bool PAIR, bool ROLLED = true>
 __device__ __forceinline__ void batch_sites(const BatchLattice &L, const float *rates, uint32_t first, uint32_t end,
                                             uint32_t step_lo, uint32_t step_hi) {
   float *__restrict__ f = static_cast<float *>(L.f);
@@ -82,7 +82,7 @@ __device__ __forceinline__ void batch_sites(const BatchLattice &L, const float *
       site_xyz(L, s0, x0, y, z);
       load_logical2<D, float, PARITY>(f, plane, addr2(x0, y, z, L.nx, L.ny, L.nz), F);
     }
-    collide_lattice<D, SHEAR>(F, L, rates, s0, 1u, step_lo, step_hi);
+    collide_lattice<D, SHEAR, ROLLED>(F, L, rates, s0, 1u, step_lo, step_hi);
     // The neighbour addresses (18 registers) are rebuilt from the site index for the
     // store instead of being kept across the collision; the empty asm hides s0's
     // provenance so that the compiler cannot merge the two computations.
@@ -106,7 +106,7 @@ __device__ __forceinline__ void batch_sites(const BatchLattice &L, const float *
 #pragma unroll
       for (int a = 0; a < 27; ++a) set_lane((&F[0][0][0])[a], l, (&Fl[0][0][0])[a]);
     }
-    collide_lattice<D, SHEAR>(F, L, rates, s0, T, step_lo, step_hi);
+    collide_lattice<D, SHEAR, ROLLED>(F, L, rates, s0, T, step_lo, step_hi);
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
       if (l == 1 && !second) break;
@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) batch_kernel(const BatchA
 // is read from the device counter plus `k`, so that a captured graph of n such launches
 // serves every call with the same n and the same starting parity; PARITY is fixed per
 // launch.
-template <int D, bool SHEAR, int PARITY>
-__global__ void __launch_bounds__(kBatchMaxThreads, 2)
+template <int D, bool SHEAR, int PARITY, bool ROLLED, int MINB>
+__global__ void __launch_bounds__(MINB >= 5 ? 128 : kBatchMaxThreads, MINB)
     batch_step_kernel(const BatchArgs a, int k, int lat_lo, int lat_hi, int tile_base) {
   const int t = tile_base + (int)blockIdx.x;
   const int lat = lattice_of(a, t, lat_lo, lat_hi);
@@ -228,9 +228,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2)
   const unsigned long long step = (unsigned long long)(*a.step_counter + k);
   const float *rates = a.rates + 54 * lat;
   if (L.nx % 2 == 0)
-    batch_sites<D, PARITY, SHEAR, true>(L, rates, first, end, (uint32_t)step, (uint32_t)(step >> 32));
+    batch_sites<D, PARITY, SHEAR, true, ROLLED>(L, rates, first, end, (uint32_t)step, (uint32_t)(step >> 32));
   else
-    batch_sites<D, PARITY, SHEAR, false>(L, rates, first, end, (uint32_t)step, (uint32_t)(step >> 32));
+    batch_sites<D, PARITY, SHEAR, false, ROLLED>(L, rates, first, end, (uint32_t)step, (uint32_t)(step >> 32));
 }
 
 // Advances the shared step counter after the n step launches of one call.
@@ -243,26 +243,37 @@ cudaError_t batch_max_blocks(bool shear, int threads, int *blocks_per_sm) {
                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<false>, threads, 0);
 }
 
+// Launch shapes of the per-step form (BatchForm): register cap 128 (up to 256 threads,
+// two blocks per SM) or 102 (up to 128 threads, five blocks per SM), D3Q27 noise loop
+// unrolled or rolled (D2Q9 has no loop).
 template <int D, bool SHEAR, int PARITY>
-cudaError_t launch_group(const BatchArgs &a, int k, const BatchGroup &g, int threads, cudaStream_t s) {
-  if (g.ntiles > 0) batch_step_kernel<D, SHEAR, PARITY><<<g.ntiles, threads, 0, s>>>(a, k, g.lat_lo, g.lat_hi, g.tile0);
+cudaError_t launch_group(int form, const BatchArgs &a, int k, const BatchGroup &g, int threads, cudaStream_t s) {
+  if (g.ntiles <= 0) return cudaSuccess;
+  if (form == kBatchStepOcc)
+    batch_step_kernel<D, SHEAR, PARITY, false, 5><<<g.ntiles, threads, 0, s>>>(a, k, g.lat_lo, g.lat_hi, g.tile0);
+  else if (form == kBatchStepRolled)  // D2Q9 has no noise loop: the same kernel as form 0
+    batch_step_kernel<D, SHEAR, PARITY, D == 3, 2><<<g.ntiles, threads, 0, s>>>(a, k, g.lat_lo, g.lat_hi, g.tile0);
+  else
+    batch_step_kernel<D, SHEAR, PARITY, false, 2><<<g.ntiles, threads, 0, s>>>(a, k, g.lat_lo, g.lat_hi, g.tile0);
   return cudaGetLastError();
 }
 
 template <int D>
-cudaError_t launch_group_any(bool shear, int parity, const BatchArgs &a, int k, const BatchGroup &g, int threads,
-                             cudaStream_t s) {
+cudaError_t launch_group_any(int form, bool shear, int parity, const BatchArgs &a, int k, const BatchGroup &g,
+                             int threads, cudaStream_t s) {
   if (shear)
-    return parity ? launch_group<D, true, 1>(a, k, g, threads, s) : launch_group<D, true, 0>(a, k, g, threads, s);
-  return parity ? launch_group<D, false, 1>(a, k, g, threads, s) : launch_group<D, false, 0>(a, k, g, threads, s);
+    return parity ? launch_group<D, true, 1>(form, a, k, g, threads, s)
+                  : launch_group<D, true, 0>(form, a, k, g, threads, s);
+  return parity ? launch_group<D, false, 1>(form, a, k, g, threads, s)
+                : launch_group<D, false, 0>(form, a, k, g, threads, s);
 }
 
-cudaError_t launch_batch_steps(bool shear, int parity0, const BatchArgs &a, const BatchGroup &g3,
+cudaError_t launch_batch_steps(int form, bool shear, int parity0, const BatchArgs &a, const BatchGroup &g3,
                                const BatchGroup &g2, int n, int threads, cudaStream_t s) {
   for (int k = 0; k < n; ++k) {
     const int parity = (parity0 + k) & 1;
-    cudaError_t e = launch_group_any<3>(shear, parity, a, k, g3, threads, s);
-    if (e == cudaSuccess) e = launch_group_any<2>(shear, parity, a, k, g2, threads, s);
+    cudaError_t e = launch_group_any<3>(form, shear, parity, a, k, g3, threads, s);
+    if (e == cudaSuccess) e = launch_group_any<2>(form, shear, parity, a, k, g2, threads, s);
     if (e != cudaSuccess) return e;
   }
   batch_advance_kernel<<<1, 1, 0, s>>>(a.step_counter, n);

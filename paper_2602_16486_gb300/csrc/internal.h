@@ -58,9 +58,17 @@ cudaError_t launch_batch(bool shear, const BatchArgs &a, int grid, int threads, 
 struct BatchGroup {
   int lat_lo, lat_hi, tile0, ntiles;
 };
+// Launch forms of a batch (values of flbm_batch_set_shape's `form`).
+enum BatchForm {
+  kBatchStep = 0,        // per-step launches, 128-register cap, unrolled D3Q27 noise
+  kBatchPersistent = 1,  // one cooperative launch, per-lattice completion counters
+  kBatchStepOcc = 2,     // per-step launches, 102-register cap (five blocks of <= 128)
+  kBatchStepRolled = 3,  // per-step launches, 128-register cap, rolled D3Q27 noise
+  kBatchFormMax = 3
+};
 // n steps as plain launches (per step one launch per lattice type, block = tile), then
 // the step-counter update.
-cudaError_t launch_batch_steps(bool shear, int parity0, const BatchArgs &a, const BatchGroup &g3,
+cudaError_t launch_batch_steps(int form, bool shear, int parity0, const BatchArgs &a, const BatchGroup &g3,
                                const BatchGroup &g2, int n, int threads, cudaStream_t s);
 
 // Statistics accumulators, in doubles: see stats.cu for the layout.

@@ -117,10 +117,8 @@ def _load():
         "flbm_batch_lattice": (vp, [vp, ctypes.c_int]),
         "flbm_batch_step": (ctypes.c_int, [vp, ctypes.c_int64]),
         "flbm_batch_get_step": (ctypes.c_int64, [vp]),
-        "flbm_batch_set_threads": (ctypes.c_int, [vp, ctypes.c_int]),
-        "flbm_batch_get_threads": (ctypes.c_int, [vp]),
-        "flbm_batch_set_persistent": (ctypes.c_int, [vp, ctypes.c_int]),
-        "flbm_batch_get_persistent": (ctypes.c_int, [vp]),
+        "flbm_batch_set_shape": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+        "flbm_batch_get_shape": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "flbm_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int)]),
         "flbm_batch_uses_graph": (ctypes.c_int, [vp]),
@@ -362,28 +360,26 @@ def flbm_batch_get_step(b):
     return int(_lib.flbm_batch_get_step(b))
 
 
-def flbm_batch_set_threads(b, threads):
-    _check(_lib.flbm_batch_set_threads(b, int(threads)))
+FLBM_BATCH_STEP, FLBM_BATCH_PERSISTENT, FLBM_BATCH_STEP_OCC, FLBM_BATCH_STEP_ROLLED = 0, 1, 2, 3
 
 
-def flbm_batch_get_threads(b):
-    return int(_lib.flbm_batch_get_threads(b))
+def flbm_batch_set_shape(b, threads, form):
+    _check(_lib.flbm_batch_set_shape(b, int(threads), int(form)))
 
 
-def flbm_batch_set_persistent(b, persistent):
-    _check(_lib.flbm_batch_set_persistent(b, int(bool(persistent))))
-
-
-def flbm_batch_get_persistent(b):
-    return int(_lib.flbm_batch_get_persistent(b))
+def flbm_batch_get_shape(b):
+    t = ctypes.c_int(-1)
+    f = ctypes.c_int(-1)
+    _check(_lib.flbm_batch_get_shape(b, ctypes.byref(t), ctypes.byref(f)))
+    return t.value, f.value
 
 
 def flbm_batch_autotune(b, trial_steps=10):
-    """Returns (threads, persistent) of the fastest launch shape."""
+    """Returns (threads, form) of the fastest launch shape."""
     t = ctypes.c_int(-1)
-    p = ctypes.c_int(-1)
-    _check(_lib.flbm_batch_autotune(b, int(trial_steps), ctypes.byref(t), ctypes.byref(p)))
-    return t.value, bool(p.value)
+    f = ctypes.c_int(-1)
+    _check(_lib.flbm_batch_autotune(b, int(trial_steps), ctypes.byref(t), ctypes.byref(f)))
+    return t.value, f.value
 
 
 def flbm_batch_uses_graph(b):
@@ -511,20 +507,13 @@ class Batch:
         return flbm_batch_get_step(self.handle)
 
     @property
-    def threads(self):
-        return flbm_batch_get_threads(self.handle)
+    def shape(self):
+        """(threads per block, launch form)."""
+        return flbm_batch_get_shape(self.handle)
 
-    @threads.setter
-    def threads(self, t):
-        flbm_batch_set_threads(self.handle, t)
-
-    @property
-    def persistent(self):
-        return flbm_batch_get_persistent(self.handle) == 1
-
-    @persistent.setter
-    def persistent(self, p):
-        flbm_batch_set_persistent(self.handle, p)
+    @shape.setter
+    def shape(self, tf):
+        flbm_batch_set_shape(self.handle, tf[0], tf[1])
 
     def autotune(self, trial_steps=10):
         return flbm_batch_autotune(self.handle, trial_steps)
