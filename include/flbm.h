@@ -314,8 +314,19 @@ int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads, int *form)
 int flbm_batch_uses_graph(const flbm_batch *b);
 
 /* Wait for the batch's stream; FLBM_ETIMEOUT if a bounded wait of the persistent form
- * gave up (the flag is cleared), FLBM_ECUDA for an asynchronous device error. */
+ * gave up (the flag is cleared, and the step count is reset to the last completed
+ * launch: the populations are not valid until re-initialised or loaded), FLBM_ECUDA for
+ * an asynchronous device error. */
 int flbm_batch_sync(flbm_batch *b);
+
+/*
+ * flbm_batch_test_wait_timeout - test hook (the paper has no counterpart): the next
+ * flbm_batch_step, if it runs the persistent form, waits for completion counts that are
+ * never reached, and each wait gives up after `polls` polls (about a microsecond each),
+ * exactly as a real stall would; flbm_batch_sync then returns FLBM_ETIMEOUT. Exercises the
+ * timeout path without faulting or hanging the GPU. The hook disarms after one call.
+ */
+int flbm_batch_test_wait_timeout(flbm_batch *b, uint32_t polls);
 
 #ifdef __cplusplus
 }

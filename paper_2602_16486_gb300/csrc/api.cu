@@ -731,6 +731,7 @@ struct flbm_batch {
   int64_t step = 0;
   BatchArgs *args = nullptr;  // by-value kernel arguments (large: heap)
   bool graphs_ok = true;      // capture worked (or was not tried yet)
+  uint32_t test_wait_polls = 0;  // armed by flbm_batch_test_wait_timeout for one launch
   bool last_graph = false;
   std::map<int64_t, cudaGraphExec_t> graphs;  // per (n, form, start parity), current shape
 };
@@ -851,6 +852,8 @@ int batch_enqueue(flbm_batch *b, int64_t n) {
   b->args->done = b->d_done;
   b->args->exits = b->d_exits;
   b->args->status = b->d_status;
+  b->args->target_bias = b->test_wait_polls ? (1 << 30) : 0;
+  b->args->wait_polls = b->test_wait_polls ? b->test_wait_polls : kBatchWaitPolls;
   if (b->form != kBatchPersistent) {
     FLBM_CUDA(launch_batch_steps(b->form, b->shear, int(b->step & 1), *b->args, b->g3, b->g2, int(n), b->threads,
                                  b->stream));
@@ -1017,7 +1020,8 @@ int flbm_batch_step(flbm_batch *b, int64_t n) {
   }
   int st = batch_shape(b);
   if (st != FLBM_OK) return st;
-  cudaGraphExec_t exec = batch_graph(b, n);
+  // An armed test hook changes the kernel arguments of this one launch: no graph.
+  cudaGraphExec_t exec = b->test_wait_polls ? nullptr : batch_graph(b, n);
   b->last_graph = exec != nullptr;
   if (exec) {
     FLBM_CUDA(cudaGraphLaunch(exec, b->stream));
@@ -1025,6 +1029,7 @@ int flbm_batch_step(flbm_batch *b, int64_t n) {
     st = batch_enqueue(b, n);
     if (st != FLBM_OK) return st;
   }
+  b->test_wait_polls = 0;
   b->step += n;
   for (flbm_ctx *c : b->members) c->step = b->step;
   return FLBM_OK;
@@ -1062,9 +1067,23 @@ int flbm_batch_sync(flbm_batch *b) {
   int h = 0;
   FLBM_CUDA(cudaMemcpy(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (h != 0) {
+    // The failed launch did not advance the device step counter: take it as the step
+    // count, so that the batch stays usable (re-initialise or load checkpoints).
+    long long dev_step = 0;
+    FLBM_CUDA(cudaMemcpy(&dev_step, b->d_step, sizeof(long long), cudaMemcpyDeviceToHost));
     FLBM_CUDA(cudaMemset(b->d_status, 0, sizeof(int)));
-    return fail(FLBM_ETIMEOUT, "a bounded wait of the batch kernel gave up; the state is not valid");
+    b->step = dev_step;
+    for (flbm_ctx *c : b->members) c->step = dev_step;
+    return fail(FLBM_ETIMEOUT, "a bounded wait of the batch kernel gave up; the populations are not valid "
+                               "(step count reset to %lld)", dev_step);
   }
+  return FLBM_OK;
+}
+
+int flbm_batch_test_wait_timeout(flbm_batch *b, uint32_t polls) {
+  if (!b) return fail(FLBM_EINVAL, "batch is NULL");
+  if (polls == 0) return fail(FLBM_EINVAL, "polls must be >= 1");
+  b->test_wait_polls = polls;
   return FLBM_OK;
 }
 

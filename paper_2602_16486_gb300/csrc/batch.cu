@@ -27,7 +27,7 @@
 // advanced by the last block to leave, so that one captured graph of the launch serves
 // every call with the same n.
 //
-// Every wait is bounded: a block that polls longer than kWaitSpin times (or sees another
+// Every wait is bounded: a block that polls longer than wait_polls times (or sees another
 // block's failure) sets the status word and leaves; the host reports FLBM_ETIMEOUT.
 #include <cuda_runtime.h>
 
@@ -37,7 +37,6 @@
 namespace flbm {
 namespace {
 
-constexpr uint32_t kWaitSpin = 1u << 22;  // polls of about a microsecond each
 
 // The collision with lattice L's parameters: its three shear-structure numbers (SHEAR:
 // per-mode factors are compile-time constants) or its per-mode arrays; round keys are
@@ -137,9 +136,9 @@ __device__ __forceinline__ void batch_tile(const BatchLattice &L, const float *r
 }
 
 // Thread 0: waits until lattice `lat` has finished `target` tiles in this launch.
-__device__ __forceinline__ bool wait_done(const int *done, int target, int *status) {
+__device__ __forceinline__ bool wait_done(const int *done, int target, int *status, uint32_t polls) {
   const volatile int *d = done;
-  for (uint32_t it = 0; it < kWaitSpin; ++it) {
+  for (uint32_t it = 0; it < polls; ++it) {
     if (*d >= target) return true;
     if (*(volatile int *)status != 0) return false;
     __nanosleep(32);
@@ -178,7 +177,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) batch_kernel(const BatchA
     const BatchLattice &L = a.lats[lat];
     if (threadIdx.x == 0) {
       int ok = 1;
-      if (s > 0) ok = wait_done(&a.done[lat], s * tiles_of(a, lat), a.status);
+      if (s > 0) ok = wait_done(&a.done[lat], s * tiles_of(a, lat) + a.target_bias, a.status, a.wait_polls);
       __threadfence();  // acquire: the lattice's step s - 1 writes are visible
       s_ok = ok;
     }

@@ -31,6 +31,7 @@ struct StepArgs {
 constexpr int kBatchMaxThreads = 256;  // largest tile: 512 sites (two per thread)
 
 constexpr int kBatchMaxLattices = 512;  // bound of the by-value lattice table below
+constexpr uint32_t kBatchWaitPolls = 1u << 22;  // polls of about a microsecond each
 
 struct BatchLattice {  // one lattice of a batch (FP32 storage); lives in the kernel arguments
   void *f;
@@ -49,6 +50,8 @@ struct BatchArgs {
   int *done;                 // device, one per lattice, zero at launch: tiles finished
   unsigned int *exits;       // device, zero at launch: blocks that have left
   int *status;               // nonzero after a bounded wait gave up
+  int target_bias;           // added to every completion target (0; a test hook raises it)
+  uint32_t wait_polls;       // bound of each wait, in polls
   BatchLattice lats[kBatchMaxLattices];
 };
 cudaError_t batch_max_blocks(bool shear, int threads, int *blocks_per_sm);

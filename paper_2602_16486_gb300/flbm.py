@@ -123,6 +123,7 @@ def _load():
                                                ctypes.POINTER(ctypes.c_int)]),
         "flbm_batch_uses_graph": (ctypes.c_int, [vp]),
         "flbm_batch_sync": (ctypes.c_int, [vp]),
+        "flbm_batch_test_wait_timeout": (ctypes.c_int, [vp, ctypes.c_uint32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -388,6 +389,10 @@ def flbm_batch_uses_graph(b):
 
 def flbm_batch_sync(b):
     _check(_lib.flbm_batch_sync(b))
+
+
+def flbm_batch_test_wait_timeout(b, polls):
+    _check(_lib.flbm_batch_test_wait_timeout(b, int(polls)))
 
 
 # ---- a thin owner object over the same calls ---------------------------------------------

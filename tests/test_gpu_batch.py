@@ -235,3 +235,32 @@ def test_batch_invalid_specs(fl):
         b.step(0)
         assert b.step_count == 0
         assert fl.flbm_batch_uses_graph(b.handle) in (0, 1)
+
+
+def test_persistent_wait_timeout_reported_and_recoverable(fl):
+    # The persistent form's completion waits are bounded: a launch whose waits can never
+    # be satisfied (test hook) gives up after 2000 polls per wait, reports FLBM_ETIMEOUT at
+    # the next sync, leaves the step count at the last completed launch, and the batch
+    # keeps working afterwards. No GPU fault, trap or hang is involved.
+    specs = _specs(False)
+    with fl.Batch(specs) as b:
+        _init(b)
+        b.shape = (128, 1)
+        fl.flbm_batch_test_wait_timeout(b.handle, 2000)
+        b.step(3)
+        with pytest.raises(fl.FlbmError) as e:
+            b.sync()
+        assert e.value.status == fl.FLBM_ETIMEOUT
+        assert b.step_count == 0
+        f0 = _init(b)  # allowed again at step 0
+        b.step(5)
+        b.sync()
+        got = [b.lattice(i).populations() for i in range(len(specs))]
+    with fl.Batch(specs) as b:
+        ref0 = _init(b)
+        b.step(5)
+        ref = [b.lattice(i).populations() for i in range(len(specs))]
+    for x, y in zip(f0, ref0):
+        assert np.array_equal(x, y)
+    for x, y in zip(got, ref):
+        assert np.array_equal(x, y)

@@ -239,3 +239,32 @@ def test_storage_precision_against_oracle_replica(fl, kbt, oracle_mod):
               f"max mode-variance error {e_kk:.2e}")
         assert abs(e_uu) <= tol, (storage, e_uu)
         assert e_kk <= tol, (storage, kk[noisy] / kk_ref[noisy])
+
+
+def test_c1_statistics_follow_the_oracle(fl, oracle_mod):
+    # Config 1: D2Q9 64x64 at rest, kBT 1e-4, every non-conserved mode at rate 1.25
+    # (tau 0.8), seed 42, 1000 steps. The GPU (FP32) and the oracle (FP64) run the same
+    # noise, so their sampled <u_a^2> and mode variances agree sample by sample.
+    lam = np.full(9, 1.25)
+    lam[:3] = 1.0
+    dims = (64, 64, 1)
+    every = 50
+    with fl.Lattice(0, dims, lam, 1e-4, 1.0, 42) as lat:
+        fo = lat.populations()
+        worst_u, worst_k, ratios = 0.0, 0.0, []
+        for k in range(0, 1001, every):
+            if k >= 100:
+                sg = lat.stats()
+                so = oracle_mod.stats(0, dims, fo)
+                du = np.abs(np.array(sg["uu"][:2]) - so["uu"][:2]) / so["uu"][:2]
+                dk = np.abs(np.diag(sg["k_cov"])[3:9] - np.diag(so["k_cov"])[3:9]) / np.diag(so["k_cov"])[3:9]
+                worst_u, worst_k = max(worst_u, du.max()), max(worst_k, dk.max())
+                ratios.append(so["uu"][:2].mean() / _target(1e-4))
+            if k < 1000:
+                lat.step(every)
+                fo = oracle_mod.run(0, dims, lam, 1e-4, 42, fo, k, every)
+    print(f"C1: GPU vs oracle, worst relative difference <u^2> {worst_u:.1e}, mode variances {worst_k:.1e}; "
+          f"oracle <u^2>/target averaged over steps 100-1000: {np.mean(ratios):.4f}")
+    assert worst_u <= 1e-4 and worst_k <= 1e-4
+    # 4096 sites x 19 samples: the 3-sigma sampling error of the average is about 3 %
+    assert abs(np.mean(ratios) - 1.0) <= 0.05
