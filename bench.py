@@ -158,6 +158,23 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+def max_over_ranks(x, world, device):
+    """Largest value of x over the ranks (the job's time is the slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_glups(world, sites_per_rank, steps, elapsed_s):
+    """Whole-job throughput: every rank's site updates over the slowest rank's time."""
+    return world * sites_per_rank * steps / elapsed_s / 1e9
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -235,12 +252,7 @@ def run_ours(args):
     step_kernel_ms = [a.elapsed_time(b) for a, b in ev_k]
     samples = lat.fetch_samples()
     nonfinite = sum(s["nonfinite"] for s in samples)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, world, "cuda")
 
     # ---- end to end through the C ABI with host buffers ---------------------------------
     if args.no_e2e:
@@ -267,12 +279,7 @@ def run_ours(args):
             stats_bytes += (14 + 27 + 27 * 28 // 2 + 1) * 8
     fl.flbm_save(lat.ctx, host_out.data_ptr(), nbytes)
     e2e_s = time.perf_counter() - w0
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, "cuda")
     lat.close()
 
     if rank != 0:
@@ -282,7 +289,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return None
 
-    value = world * sites * args.steps / (elapsed_ms * 1e-3) / 1e9
+    value = job_glups(world, sites, args.steps, elapsed_ms * 1e-3)
     avg_kernel_ms = float(np.mean(step_kernel_ms))
     peaks, peak_kind = measured_peaks()
     achieved = BYTES_PER_SITE * sites / (avg_kernel_ms * 1e-3) / 1e9
@@ -314,7 +321,7 @@ def run_ours(args):
         "config": dict(workload_config(S, world, dims), step_variant=variant),
         "roofline": roof,
         "e2e": {
-            "value": round(world * sites * n_e2e / e2e_s / 1e9, 3),
+            "value": round(job_glups(world, sites, n_e2e, e2e_s), 3),
             "unit": UNIT,
             "h2d_bytes_per_step": int(nbytes / n_e2e),
             "d2h_bytes_per_step": int((nbytes + stats_bytes) / n_e2e),
