@@ -188,15 +188,15 @@ int flbm_load(flbm_ctx *ctx, const void *host, size_t bytes);
  *   out             : host struct, written on FLBM_OK and FLBM_ENUMERIC; out->step is
  *                     -1 (the array carries no step count).
  * Scratch: the FP64 accumulators live in one statically allocated device array of
- * FLBM_NOALLOC_SCRATCH_DOUBLES doubles (4 KiB), which every GPU that loads the library
+ * FLBM_NOALLOC_SCRATCH_DOUBLES doubles (8 KiB), which every GPU that loads the library
  * keeps until the process exits. A lattice whose accumulators would not fit is rejected
- * with FLBM_EINVAL (D2Q9 needs 69 doubles, D3Q27 420). The first call on a device looks
+ * with FLBM_EINVAL (D2Q9 needs 137 doubles, D3Q27 529). The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) and caches it; make that first
  * call before any stream capture. Every call reuses the same array and zeroes it first,
  * so calls whose GPU work overlaps (other streams, other host threads) race and return
  * wrong sums: serialise them.
  */
-#define FLBM_NOALLOC_SCRATCH_DOUBLES 512
+#define FLBM_NOALLOC_SCRATCH_DOUBLES 1024
 int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storage, int parity, double rho0,
                        const void *dev_populations, void *cuda_stream, flbm_stats_t *out);
 

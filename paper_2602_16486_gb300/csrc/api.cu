@@ -12,6 +12,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/flbm.h"
@@ -183,30 +184,47 @@ int ensure_stage(flbm_ctx *c, size_t elems) {
   return FLBM_OK;
 }
 
-// Host struct from one record of accumulators (layout in stats.cu).
+// Host struct from one record: the upper triangle of the Gram matrix G of the per-site
+// column c = [1, rho - rho0, j, u, k_{D+1} .. k_{Q-1}, 0 ...] (NC columns; stats.cu),
+// then the non-finite count. k_0 = rho = rho0 + (rho - rho0) is rebuilt in FP64; the
+// central moments k_1..k_D vanish identically and are reported as 0.
 void fill_stats(const flbm_ctx *c, const double *acc, int64_t step, flbm_stats_t *out) {
-  const int Q = c->Q;
-  const int nacc = stats_nacc(Q);
+  const int Q = c->Q, D = c->D;
+  const int NC = D == 3 ? 32 : 16;
+  auto G = [&](int a, int b) {
+    if (a > b) std::swap(a, b);
+    return acc[a * NC - a * (a - 1) / 2 + (b - a)];
+  };
   std::memset(out, 0, sizeof(*out));
   out->step = step;
   out->sites = c->N;
   out->lattice = c->lattice;
   out->q = Q;
-  out->nonfinite = (int64_t)llround(acc[nacc]);
+  out->nonfinite = (int64_t)llround(acc[NC * (NC + 1) / 2]);
   const double inv = 1.0 / double(c->N);
-  out->mass = c->rho0 * acc[0] + acc[1];
+  const double rho0 = c->rho0, cnt = G(0, 0), sd = G(0, 1);
+  out->mass = rho0 * cnt + sd;
   for (int a = 0; a < 3; ++a) {
-    out->mom[a] = acc[2 + a];
-    out->u_mean[a] = acc[5 + a] * inv;
+    out->mom[a] = G(0, 2 + a);
+    out->u_mean[a] = G(0, 5 + a) * inv;
   }
-  for (int a = 0; a < 6; ++a) out->uu[a] = acc[8 + a] * inv;
-  for (int v = 0; v < Q; ++v) out->k_mean[v] = acc[14 + v] * inv;
-  int e = 14 + Q;
-  for (int v = 0; v < Q; ++v)
-    for (int w = v; w < Q; ++w, ++e) {
-      out->k_cov[v * Q + w] = acc[e] * inv;
-      out->k_cov[w * Q + v] = acc[e] * inv;
+  const int uu_pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  for (int e = 0; e < 6; ++e) out->uu[e] = G(5 + uu_pairs[e][0], 5 + uu_pairs[e][1]) * inv;
+  // column of mode v >= D + 1
+  auto kc = [&](int v) { return 8 + v - D - 1; };
+  out->k_mean[0] = (rho0 * cnt + sd) * inv;
+  for (int v = D + 1; v < Q; ++v) out->k_mean[v] = G(0, kc(v)) * inv;
+  out->k_cov[0] = (rho0 * rho0 * cnt + 2.0 * rho0 * sd + G(1, 1)) * inv;
+  for (int v = D + 1; v < Q; ++v) {
+    const double k0v = (rho0 * G(0, kc(v)) + G(1, kc(v))) * inv;
+    out->k_cov[v] = k0v;
+    out->k_cov[v * Q] = k0v;
+    for (int w = v; w < Q; ++w) {
+      const double vw = G(kc(v), kc(w)) * inv;
+      out->k_cov[v * Q + w] = vw;
+      out->k_cov[w * Q + v] = vw;
     }
+  }
 }
 
 int enqueue_stats(flbm_ctx *c, double *acc_dev) {
@@ -1227,6 +1245,7 @@ extern "C" int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storag
   // The host conversion of flbm_stats, fed with a description of this array.
   flbm_ctx view;
   view.lattice = lattice;
+  view.D = d_of(lattice);
   view.Q = Q;
   view.N = N;
   view.rho0 = rho0;

@@ -3,87 +3,87 @@
 // the central-moment means and covariances whose equilibrium form is C^eq (Sec. II-B,
 // "Structural properties"), plus mass and momentum for the conservation checks.
 //
-// Output record (doubles, read by the host in api.cu):
-//   [0] number of finite sites         [1] sum (rho - rho0)   [2..4] sum j
-//   [5..7] sum u                        [8..13] sum u_a u_b (xx, yy, zz, xy, xz, yz)
-//   [14 .. 14+Q) sum k_v                then sum k_v k_w for v <= w (row-major upper)
-//   [nacc] number of non-finite sites
-//
 // Every one of these sums is an entry of the Gram matrix G = sum_x c(x) c(x)^T of the
-// per-site column vector
-//   c = [1, rho - rho0, j_x, j_y, j_z, u_x, u_y, u_z, k_0 .. k_{Q-1}, 0 ...]
-// (row 0 of G gives the linear sums). Persistent blocks of 128 threads walk tiles of 256
-// sites; each thread computes two sites with the packed FP32x2 algebra of the step
-// (cm.cuh) and writes their columns as (site a, site b) pairs to shared memory. The
-// needed 4 x 4 blocks of G are then accumulated in registers, each packed FMA adding one
-// entry for both sites of a pair; per-tile sums collect in shared memory in FP32, go to
-// FP64 (also in shared memory) every 8 tiles and to the output with one FP64 atomic per
-// entry and block. Sites with a non-finite value
-// contribute a zero column and are counted.
+// per-site column vector (NC = 32 entries for D3Q27, 16 for D2Q9)
+//   c = [1, rho - rho0, j_x, j_y, j_z, u_x, u_y, u_z, k_{D+1} .. k_{Q-1}, 0 ...]
+// (row 0 of G gives the linear sums; k_0 = rho and the central moments k_1..k_D, which
+// vanish identically, are rebuilt or set to zero by the host). The output record is the
+// upper triangle of G in FP64, row-major, followed by the number of non-finite sites;
+// api.cu maps it to flbm_stats_t.
+//
+// G is a dense contraction over the sites, so it runs on the tensor cores (warp-level
+// mma.sync m16n8k8 with TF32 inputs and FP32 accumulation). Each input x is split into
+// x_hi = tf32(x) and x_lo = tf32(x - x_hi) and every product is formed as
+// hi*hi + hi*lo + lo*hi, which keeps about 2^-21 relative accuracy per product (the
+// three-pass TF32 scheme). Persistent blocks of 128 threads walk tiles of 256 sites:
+// each thread computes two sites with the packed FP32x2 algebra of the step (cm.cuh)
+// and writes their split columns to shared memory (swizzled rows, conflict-free); each
+// warp then accumulates the upper block-triangle of G over 64 sites of the tile in FP32
+// fragments, adds them to the block's FP64 sums (shared memory) every 8 tiles and, at
+// the end, the block adds its sums to the output with one FP64 atomic per entry. Sites with a non-finite value contribute a zero column and are
+// counted.
 #include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "cm.cuh"
 #include "internal.h"
 
 namespace flbm {
 
-int stats_nacc(int Q) { return 14 + Q + Q * (Q + 1) / 2; }
+template <int D>
+struct StatsPlan {
+  static constexpr int Q = Lat<D>::Q;
+  static constexpr int NC = D == 3 ? 32 : 16;  // columns, padded to whole MMA tiles
+  static constexpr int LD = 32;                // shared-memory row: 32 words, swizzled (see swz)
+  static constexpr int MT = NC / 16;           // 16-row tiles of G
+  static constexpr int NT = NC / 8;            // 8-column tiles of G
+  // Upper block-triangle: tiles (mt, nt) with nt >= 2 mt.
+  static constexpr int NTILE = D == 3 ? 6 : 2;
+  static constexpr int NREC = NC * (NC + 1) / 2;
+};
+
+int stats_nacc(int Q) { return Q == 27 ? StatsPlan<3>::NREC : StatsPlan<2>::NREC; }
 
 namespace {
 
-constexpr int kTilePairs = kStatsBlock;  // 128 threads x 2 sites = 256 sites per tile
+constexpr int kTileSites = 2 * kStatsBlock;  // 128 threads x 2 sites
+constexpr int kWarps = kStatsBlock / 32;
 constexpr int kFlushTiles = 8;
 
 template <int D>
-struct GramPlan {
-  static constexpr int Q = Lat<D>::Q;
-  static constexpr int NCOL = 8 + Q;
-  static constexpr int G = (NCOL + 3) / 4;  // column groups of 4
-  static constexpr int NC = 4 * G;
-  // Shared-memory row stride (float2): padded by 2 so that rows read at the same time by
-  // the different site-pair ranges of a warp start on different banks.
-  static constexpr int LDT = NC + 2;
-  // Needed blocks (gi, gj), gi <= gj: (0, *) linear sums, (1, 1) u u, (k, k) covariances.
-  static constexpr int NBLK = G + 1 + (G - 2) * (G - 1) / 2;
-  static constexpr int PARTS = kStatsBlock / NBLK;  // site-pair ranges per block
-};
-
+__host__ __device__ constexpr int tile_mt(int i) {
+  return D == 3 ? (i < 4 ? 0 : 1) : 0;
+}
 template <int D>
-__device__ __forceinline__ void block_of(int b, int &gi, int &gj) {
-  constexpr int G = GramPlan<D>::G;
-  if (b < G) {
-    gi = 0;
-    gj = b;
-    return;
-  }
-  if (b == G) {
-    gi = gj = 1;
-    return;
-  }
-  int r = b - G - 1;
-  gi = 2;
-  while (r >= G - gi) {
-    r -= G - gi;
-    ++gi;
-  }
-  gj = gi + r;
+__host__ __device__ constexpr int tile_nt(int i) {
+  return D == 3 ? (i < 4 ? i : i - 2) : i;
 }
 
-// Record index of Gram entry (c1, c2), c1 <= c2, or -1 if the record does not keep it.
-template <int D>
-__device__ __forceinline__ int record_index(int c1, int c2) {
-  constexpr int Q = Lat<D>::Q;
-  if (c2 >= 8 + Q) return -1;
-  if (c1 == 0) return c2 < 8 ? c2 : 14 + (c2 - 8);
-  if (c1 >= 5 && c1 <= 7 && c2 >= 5 && c2 <= 7) {
-    const int a = c1 - 5, b = c2 - 5;
-    return a == b ? 8 + a : (a == 0 ? (b == 1 ? 11 : 12) : 13);
-  }
-  if (c1 >= 8) {
-    const int v = c1 - 8, w = c2 - 8;
-    return 14 + Q + v * Q - v * (v - 1) / 2 + (w - v);
-  }
-  return -1;
+// Shared-memory rows hold 32 words; column c of row r sits at word c ^ swz(r). With
+// swz(r) = 8 (r mod 4) + 4 (bit 2 of r), the 16-byte stores of eight consecutive rows
+// and the fragment loads of an MMA step (rows s0 + t or s0 + t + 4, columns m0 + g) hit
+// 32 different banks.
+__device__ __forceinline__ int swz(int r) { return ((r & 3) << 3) | (((r >> 2) & 1) << 2); }
+
+// Round to TF32 (nearest, ties away): x_hi = tf32(x), x_lo = tf32(x - x_hi). Both are
+// rounded to nearest, so the split carries no bias (truncating x_lo would shrink every
+// product by about 2^-20 on average).
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// D (16x8, FP32) += A (16x8, TF32, row-major) * B (8x8, TF32, column-major).
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
 // Columns of the two sites of a pair (lane x: site s, lane y: site s + 1). PAIRROW: nx is
@@ -97,7 +97,8 @@ __device__ __forceinline__ void pair_columns(const S *__restrict__ f, long long 
   bool valid[2] = {s < N, s + 1 < N};
   if (PAIRROW) {
     if (valid[0]) {
-      const int x0 = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
+      const uint32_t r = (uint32_t)s / (uint32_t)nx, q = r / (uint32_t)ny;
+      const int x0 = (int)((uint32_t)s - r * (uint32_t)nx), y = (int)(r - q * (uint32_t)ny), z = (int)q;
       load_logical2<D, S, PARITY>(f, plane, addr2(x0, y, z, nx, ny, nz), F);
     } else {
 #pragma unroll
@@ -109,7 +110,8 @@ __device__ __forceinline__ void pair_columns(const S *__restrict__ f, long long 
       const long long sl = s + l;
       float Fl[3][3][3];
       if (valid[l]) {
-        const int x = (int)(sl % nx), y = (int)((sl / nx) % ny), z = (int)(sl / ((long long)nx * ny));
+        const uint32_t r = (uint32_t)sl / (uint32_t)nx, q = r / (uint32_t)ny;
+        const int x = (int)((uint32_t)sl - r * (uint32_t)nx), y = (int)(r - q * (uint32_t)ny), z = (int)q;
         load_logical<D, S, PARITY>(f, plane, neighbourhood(x, y, z, nx, ny, nz), Fl);
       } else {
 #pragma unroll
@@ -137,152 +139,212 @@ __device__ __forceinline__ void pair_columns(const S *__restrict__ f, long long 
     k[3] = vadd(F[1][0][2], F[1][2][0]);
     k[4] = vsub(F[1][0][2], F[1][2][0]);
   }
+  col[0] = make_float2(valid[0] ? 1.0f : 0.0f, valid[1] ? 1.0f : 0.0f);
+  col[1] = drho;
+  col[2] = vmul(rho, ux);
+  col[3] = vmul(rho, uy);
+  col[4] = vmul(rho, uz);
+  col[5] = ux;
+  col[6] = uy;
+  col[7] = uz;
+#pragma unroll
+  for (int v = D + 1; v < Q; ++v) col[8 + v - D - 1] = k[v];
+  // A site whose column holds a NaN or an infinity makes the sum of its entries non-
+  // finite (the entries are far below overflow); such a site contributes a zero column
+  // (select, not multiply: it may hold NaN) and is counted.
+  float2 sum = col[1];
+#pragma unroll
+  for (int c = 2; c < 8 + Q - D - 1; ++c) sum = vadd(sum, col[c]);
 #pragma unroll
   for (int l = 0; l < 2; ++l) {
-    bool ok = valid[l] && isfinite(lane(rho, l)) && isfinite(lane(ux, l)) && isfinite(lane(uy, l)) &&
-              isfinite(lane(uz, l));
+    if (valid[l] && !isfinite(lane(sum, l))) {
+      ++nonfinite;
 #pragma unroll
-    for (int v = 0; v < Q; ++v) ok = ok && isfinite(lane(k[v], l));
-    if (valid[l] && !ok) ++nonfinite;
-    // Zero the whole column of a skipped site (select, not multiply: it may hold NaN).
-    set_lane(col[0], l, ok ? 1.0f : 0.0f);
-    set_lane(col[1], l, ok ? lane(drho, l) : 0.0f);
-    set_lane(col[2], l, ok ? lane(rho, l) * lane(ux, l) : 0.0f);
-    set_lane(col[3], l, ok ? lane(rho, l) * lane(uy, l) : 0.0f);
-    set_lane(col[4], l, ok ? lane(rho, l) * lane(uz, l) : 0.0f);
-    set_lane(col[5], l, ok ? lane(ux, l) : 0.0f);
-    set_lane(col[6], l, ok ? lane(uy, l) : 0.0f);
-    set_lane(col[7], l, ok ? lane(uz, l) : 0.0f);
-#pragma unroll
-    for (int v = 0; v < Q; ++v) set_lane(col[8 + v], l, ok ? lane(k[v], l) : 0.0f);
+      for (int c = 0; c < 8 + Q - D - 1; ++c) set_lane(col[c], l, 0.0f);
+    }
   }
 }
 
 template <int D, typename S, int PARITY, bool PAIRROW>
-__global__ void __launch_bounds__(kStatsBlock, 4) stats_kernel(const S *__restrict__ f, long long plane,
+__global__ void __launch_bounds__(kStatsBlock, 3) stats_kernel(const S *__restrict__ f, long long plane,
                                                                int nx, int ny, int nz, float rho0,
                                                                double *__restrict__ acc) {
-  using P = GramPlan<D>;
-  constexpr int NC = P::NC;
-  constexpr int LDT = P::LDT;
-  constexpr int NACC = 14 + P::Q + P::Q * (P::Q + 1) / 2;
-  constexpr int NWORK = P::NBLK * P::PARTS;
-  __shared__ __align__(16) float2 tile[kTilePairs * LDT];
-  __shared__ float part32[16][NWORK];   // FP32 partial sums of the current tile group
-  __shared__ double part64[16][NWORK];  // FP64 running sums
+  using P = StatsPlan<D>;
+  constexpr int NC = P::NC, LD = P::LD, NTILE = P::NTILE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t *hi = reinterpret_cast<uint32_t *>(smem_raw);  // [row][LD] TF32 high parts
+  uint32_t *lo = hi + kTileSites * LD;                      // [row][LD] TF32 low parts
+  double *acc64 = reinterpret_cast<double *>(lo + kTileSites * LD);  // [NTILE*4][32], all warps
   __shared__ unsigned int nonfinite_block;
 
-  const int work = threadIdx.x;
-  const bool active = work < NWORK;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
   if (threadIdx.x == 0) nonfinite_block = 0u;
-  if (active) {
+  for (int e = threadIdx.x; e < NTILE * 4 * 32; e += blockDim.x) acc64[e] = 0.0;
+
+  float d[NTILE][4];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      part32[e][work] = 0.0f;
-      part64[e][work] = 0.0;
-    }
-  }
-  // This thread's Gram block and site-pair range in phase 2.
-  int gi = 0, gj = 0;
-  const int part = active ? work % P::PARTS : 0;
-  if (active) block_of<D>(work / P::PARTS, gi, gj);
-  const int p0 = part * kTilePairs / P::PARTS, p1 = (part + 1) * kTilePairs / P::PARTS;
+  for (int i = 0; i < NTILE; ++i)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) d[i][r] = 0.0f;
 
   unsigned nonfinite = 0u;
   const long long N = plane;
-  const long long tile_sites = 2LL * kTilePairs;
   int tiles_done = 0;
-  for (long long base = (long long)blockIdx.x * tile_sites; base < N; base += (long long)gridDim.x * tile_sites) {
-    // Phase 1: columns of this thread's two sites.
+  for (long long base = (long long)blockIdx.x * kTileSites; base < N; base += (long long)gridDim.x * kTileSites) {
+    // Phase 1: split columns of this thread's two sites.
     {
       float2 col[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) col[c] = make_float2(0.0f, 0.0f);
       pair_columns<D, S, PARITY, PAIRROW>(f, plane, nx, ny, nz, rho0, base + 2 * threadIdx.x, N, col,
                                           nonfinite);
-      float4 *dst = reinterpret_cast<float4 *>(tile + threadIdx.x * LDT);
+      // The two sites go to rows tid and tid + 128 (the sums do not depend on the order).
+      const int r0 = threadIdx.x, r1 = threadIdx.x + kStatsBlock;
+      uint32_t *h0 = hi + r0 * LD, *l0 = lo + r0 * LD, *h1 = hi + r1 * LD, *l1 = lo + r1 * LD;
+      const int z0 = swz(r0), z1 = swz(r1);
 #pragma unroll
-      for (int c = 0; c < NC; c += 2) dst[c / 2] = make_float4(col[c].x, col[c].y, col[c + 1].x, col[c + 1].y);
+      for (int c = 0; c < NC; c += 4) {
+        uint4 ha, hb, la, lb;
+        uint32_t *hav = &ha.x, *hbv = &hb.x, *lav = &la.x, *lbv = &lb.x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t xa = to_tf32(col[c + q].x), xb = to_tf32(col[c + q].y);
+          hav[q] = xa;
+          hbv[q] = xb;
+          lav[q] = to_tf32(col[c + q].x - __uint_as_float(xa));
+          lbv[q] = to_tf32(col[c + q].y - __uint_as_float(xb));
+        }
+        *reinterpret_cast<uint4 *>(h0 + (c ^ z0)) = ha;
+        *reinterpret_cast<uint4 *>(h1 + (c ^ z1)) = hb;
+        *reinterpret_cast<uint4 *>(l0 + (c ^ z0)) = la;
+        *reinterpret_cast<uint4 *>(l1 + (c ^ z1)) = lb;
+      }
     }
     __syncthreads();
-    // Phase 2: the thread's 4 x 4 Gram block over its range of site pairs.
-    if (active) {
-      float2 g[4][4];
+    // Phase 2: this warp's 64 sites, 8 per MMA step (the K dimension).
+#pragma unroll 1
+    for (int ks = 0; ks < 8; ++ks) {
+      const int s0 = warp * 64 + ks * 8;
+      const int ra = (s0 + t) * LD, rb = (s0 + t + 4) * LD;
+      const int za = swz(s0 + t), zb = swz(s0 + t + 4);
+      uint32_t ah[P::MT][4], al[P::MT][4], bh[P::NT][2], bl[P::NT][2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) g[i][j] = make_float2(0.0f, 0.0f);
-#pragma unroll 4
-      for (int p = p0; p < p1; ++p) {
-        const float4 *row = reinterpret_cast<const float4 *>(tile + p * LDT);
-        const float4 a01 = row[2 * gi], a23 = row[2 * gi + 1];
-        const float4 b01 = row[2 * gj], b23 = row[2 * gj + 1];
-        const float2 a[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
-                             make_float2(a23.z, a23.w)};
-        const float2 b[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w), make_float2(b23.x, b23.y),
-                             make_float2(b23.z, b23.w)};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) g[i][j] = __ffma2_rn(a[i], b[j], g[i][j]);
+      for (int mt = 0; mt < P::MT; ++mt) {
+        const int c = mt * 16 + g;
+        ah[mt][0] = hi[ra + (c ^ za)];
+        ah[mt][1] = hi[ra + ((c + 8) ^ za)];
+        ah[mt][2] = hi[rb + (c ^ zb)];
+        ah[mt][3] = hi[rb + ((c + 8) ^ zb)];
+        al[mt][0] = lo[ra + (c ^ za)];
+        al[mt][1] = lo[ra + ((c + 8) ^ za)];
+        al[mt][2] = lo[rb + (c ^ zb)];
+        al[mt][3] = lo[rb + ((c + 8) ^ zb)];
       }
-      const bool flush = (tiles_done + 1 == kFlushTiles);
+      // G is symmetric (A = K^T, B = K): the B fragment of column tile nt is the pair
+      // (a0, a2) or (a1, a3) of row tile nt / 2, already loaded.
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int nt = 0; nt < P::NT; ++nt) {
+        const int mt = nt / 2, h = nt % 2;
+        bh[nt][0] = ah[mt][h];
+        bh[nt][1] = ah[mt][h + 2];
+        bl[nt][0] = al[mt][h];
+        bl[nt][1] = al[mt][h + 2];
+      }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float t = part32[4 * i + j][work] + (g[i][j].x + g[i][j].y);
-          if (flush) {
-            part64[4 * i + j][work] += (double)t;
-            part32[4 * i + j][work] = 0.0f;
-          } else {
-            part32[4 * i + j][work] = t;
-          }
+      for (int i = 0; i < NTILE; ++i) {
+        const int mt = tile_mt<D>(i), nt = tile_nt<D>(i);
+        mma_tf32(d[i], ah[mt], bh[nt]);
+        mma_tf32(d[i], ah[mt], bl[nt]);
+        mma_tf32(d[i], al[mt], bh[nt]);
+      }
+    }
+    if (++tiles_done == kFlushTiles) {
+      tiles_done = 0;
+#pragma unroll
+      for (int i = 0; i < NTILE; ++i)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          atomicAdd(&acc64[(i * 4 + r) * 32 + lane], (double)d[i][r]);
+          d[i][r] = 0.0f;
         }
     }
-    if (++tiles_done == kFlushTiles) tiles_done = 0;
-    __syncthreads();
+    __syncthreads();  // the tile's columns are consumed before the next tile overwrites them
   }
-  if (active) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < NTILE; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c1 = 4 * gi + i, c2 = 4 * gj + j;
-        if (gi == gj && j < i) continue;  // lower half of a diagonal block
-        const int e = record_index<D>(c1, c2);
-        if (e >= 0) atomicAdd(&acc[e], part64[4 * i + j][work] + (double)part32[4 * i + j][work]);
-      }
-  }
+    for (int r = 0; r < 4; ++r) atomicAdd(&acc64[(i * 4 + r) * 32 + lane], (double)d[i][r]);
   if (nonfinite) atomicAdd(&nonfinite_block, nonfinite);
   __syncthreads();
-  if (threadIdx.x == 0 && nonfinite_block) atomicAdd(&acc[NACC], (double)nonfinite_block);
+  // Sum the warps' fragments and add the upper triangle of G to the record.
+  for (int e = threadIdx.x; e < NTILE * 4 * 32; e += blockDim.x) {
+    const int i = e / 128, r = (e / 32) % 4, ln = e % 32;
+    const int row = tile_mt<D>(i) * 16 + (ln >> 2) + (r >= 2 ? 8 : 0);
+    const int colx = tile_nt<D>(i) * 8 + 2 * (ln & 3) + (r & 1);
+    if (row > colx) continue;
+    atomicAdd(&acc[row * NC - row * (row - 1) / 2 + (colx - row)], acc64[e]);
+  }
+  if (threadIdx.x == 0 && nonfinite_block) atomicAdd(&acc[P::NREC], (double)nonfinite_block);
+}
+
+template <int D, typename S>
+size_t stats_smem() {
+  using P = StatsPlan<D>;
+  return 2 * sizeof(uint32_t) * kTileSites * P::LD + sizeof(double) * P::NTILE * 4 * 32;
+}
+
+// Resident blocks per SM for a kernel and its dynamic shared memory (cached; the
+// attribute that allows more than 48 KB is set once per kernel).
+template <typename K>
+cudaError_t stats_grid(K kernel, size_t smem, long long tiles, int *grid) {
+  static std::mutex mu;
+  static std::map<const void *, int> cache;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find((const void *)kernel);
+    if (it != cache.end()) {
+      per_sm = it->second;
+    } else {
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kStatsBlock, smem);
+      if (e != cudaSuccess) return e;
+      cache[(const void *)kernel] = per_sm;
+    }
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long cap = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  *grid = (int)(tiles < cap ? tiles : cap);
+  return cudaSuccess;
+}
+
+template <int D, typename S, int PARITY, bool PAIRROW>
+cudaError_t launch_one(const S *p, long long plane, int nx, int ny, int nz, float rho0, double *acc,
+                       cudaStream_t s) {
+  auto kernel = stats_kernel<D, S, PARITY, PAIRROW>;
+  const size_t smem = stats_smem<D, S>();
+  const long long tiles = (plane + kTileSites - 1) / kTileSites;
+  int grid = 0;
+  const cudaError_t e = stats_grid(kernel, smem, tiles, &grid);
+  if (e != cudaSuccess) return e;
+  kernel<<<grid, kStatsBlock, smem, s>>>(p, plane, nx, ny, nz, rho0, acc);
+  return cudaGetLastError();
 }
 
 template <int D, typename S>
 cudaError_t launch_typed(int parity, const void *f, long long plane, int nx, int ny, int nz,
                          float rho0, double *acc, cudaStream_t s) {
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  const long long tiles = (plane + 2LL * kTilePairs - 1) / (2LL * kTilePairs);
-  const long long cap = (long long)(sms > 0 ? sms : 1) * 4;
-  const int grid = (int)(tiles < cap ? tiles : cap);
   const S *p = static_cast<const S *>(f);
   const bool pairrow = nx % 2 == 0;
-  if (parity == 0) {
-    if (pairrow)
-      stats_kernel<D, S, 0, true><<<grid, kStatsBlock, 0, s>>>(p, plane, nx, ny, nz, rho0, acc);
-    else
-      stats_kernel<D, S, 0, false><<<grid, kStatsBlock, 0, s>>>(p, plane, nx, ny, nz, rho0, acc);
-  } else {
-    if (pairrow)
-      stats_kernel<D, S, 1, true><<<grid, kStatsBlock, 0, s>>>(p, plane, nx, ny, nz, rho0, acc);
-    else
-      stats_kernel<D, S, 1, false><<<grid, kStatsBlock, 0, s>>>(p, plane, nx, ny, nz, rho0, acc);
-  }
-  return cudaGetLastError();
+  if (parity == 0)
+    return pairrow ? launch_one<D, S, 0, true>(p, plane, nx, ny, nz, rho0, acc, s)
+                   : launch_one<D, S, 0, false>(p, plane, nx, ny, nz, rho0, acc, s);
+  return pairrow ? launch_one<D, S, 1, true>(p, plane, nx, ny, nz, rho0, acc, s)
+                 : launch_one<D, S, 1, false>(p, plane, nx, ny, nz, rho0, acc, s);
 }
 
 }  // namespace
