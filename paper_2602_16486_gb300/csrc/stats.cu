@@ -188,6 +188,17 @@ __global__ void __launch_bounds__(kStatsBlock, 3) stats_kernel(const S *__restri
 #pragma unroll
     for (int r = 0; r < 4; ++r) d[i][r] = 0.0f;
 
+  // Word offsets of this lane's A-fragment entries within its two rows (see phase 2).
+  int off[P::MT][4];
+#pragma unroll
+  for (int mt = 0; mt < P::MT; ++mt) {
+    const int c = mt * 16 + g;
+    off[mt][0] = c ^ swz(t);
+    off[mt][1] = (c + 8) ^ swz(t);
+    off[mt][2] = c ^ swz(t + 4);
+    off[mt][3] = (c + 8) ^ swz(t + 4);
+  }
+
   unsigned nonfinite = 0u;
   const long long N = plane;
   int tiles_done = 0;
@@ -222,24 +233,24 @@ __global__ void __launch_bounds__(kStatsBlock, 3) stats_kernel(const S *__restri
       }
     }
     __syncthreads();
-    // Phase 2: this warp's 64 sites, 8 per MMA step (the K dimension).
-#pragma unroll 1
+    // Phase 2: this warp's 64 sites, 8 per MMA step (the K dimension). Rows s0 + t and
+    // s0 + t + 4 (s0 a multiple of 8) have swizzles 8 t and 8 t + 4 at every step, so a
+    // lane's word offsets within the two rows are fixed (off[]), and the steps only move
+    // the row base.
+#pragma unroll 2
     for (int ks = 0; ks < 8; ++ks) {
-      const int s0 = warp * 64 + ks * 8;
-      const int ra = (s0 + t) * LD, rb = (s0 + t + 4) * LD;
-      const int za = swz(s0 + t), zb = swz(s0 + t + 4);
+      const int ra = (warp * 64 + ks * 8 + t) * LD, rb = ra + 4 * LD;
       uint32_t ah[P::MT][4], al[P::MT][4], bh[P::NT][2], bl[P::NT][2];
 #pragma unroll
       for (int mt = 0; mt < P::MT; ++mt) {
-        const int c = mt * 16 + g;
-        ah[mt][0] = hi[ra + (c ^ za)];
-        ah[mt][1] = hi[ra + ((c + 8) ^ za)];
-        ah[mt][2] = hi[rb + (c ^ zb)];
-        ah[mt][3] = hi[rb + ((c + 8) ^ zb)];
-        al[mt][0] = lo[ra + (c ^ za)];
-        al[mt][1] = lo[ra + ((c + 8) ^ za)];
-        al[mt][2] = lo[rb + (c ^ zb)];
-        al[mt][3] = lo[rb + ((c + 8) ^ zb)];
+        ah[mt][0] = hi[ra + off[mt][0]];
+        ah[mt][1] = hi[ra + off[mt][1]];
+        ah[mt][2] = hi[rb + off[mt][2]];
+        ah[mt][3] = hi[rb + off[mt][3]];
+        al[mt][0] = lo[ra + off[mt][0]];
+        al[mt][1] = lo[ra + off[mt][1]];
+        al[mt][2] = lo[rb + off[mt][2]];
+        al[mt][3] = lo[rb + off[mt][3]];
       }
       // G is symmetric (A = K^T, B = K): the B fragment of column tile nt is the pair
       // (a0, a2) or (a1, a3) of row tile nt / 2, already loaded.
