@@ -93,6 +93,8 @@ Lattice make_d3q27() {
   return L;
 }
 
+// Lattice ids: 0 D2Q9, 1 D3Q27, 2 D3Q27 with the isotropic normal-stress modes (same
+// velocities and weights as 1; see basis_d3q27_iso).
 const Lattice &lattice(int id) {
   static const Lattice d2q9 = make_d2q9();
   static const Lattice d3q27 = make_d3q27();
@@ -155,8 +157,28 @@ double basis_d3q27(int v, double x, double y, double z) {
   return 0.0;
 }
 
+// Isotropic variant of the D3Q27 basis (the reading that resolves the anisotropy of
+// Sec. II-C, where the normal-stress modes 4-6 relax at rate 1 while the shear modes 7-9
+// relax at omega): modes 4-6 are replaced by the trace and two deviators of the same
+// second-order space,
+//   M4' = M4 + M5 + M6,  M5' = M4 - M5,  M6' = M4 + M5 - 2 M6,
+// which stay mutually orthogonal (M4..M6 have equal norms 2/9), with norms 2/3, 4/9, 4/3.
+// Relaxing M5', M6' at the shear rate gives one viscosity for every shear direction; M4'
+// carries the bulk rate. Every other mode is the paper's.
+double basis_d3q27_iso(int v, double x, double y, double z) {
+  const double a = basis_d3q27(4, x, y, z), b = basis_d3q27(5, x, y, z), c = basis_d3q27(6, x, y, z);
+  switch (v) {
+    case 4: return a + b + c;
+    case 5: return a - b;
+    case 6: return a + b - 2.0 * c;
+  }
+  return basis_d3q27(v, x, y, z);
+}
+
 double basis(int lat, int v, const double cbar[3]) {
-  return lat == 0 ? basis_d2q9(v, cbar[0], cbar[1]) : basis_d3q27(v, cbar[0], cbar[1], cbar[2]);
+  if (lat == 0) return basis_d2q9(v, cbar[0], cbar[1]);
+  if (lat == 2) return basis_d3q27_iso(v, cbar[0], cbar[1], cbar[2]);
+  return basis_d3q27(v, cbar[0], cbar[1], cbar[2]);
 }
 
 // T_vi(u) = M_v(c_i - u): the basis with every c replaced by c-bar (Sec. II-B).
