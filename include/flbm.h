@@ -33,8 +33,15 @@ extern "C" {
 typedef struct flbm_ctx flbm_ctx;
 typedef struct flbm_batch flbm_batch;
 
-/* Lattices: D2Q9 (Sec. II-B) and D3Q27 (Sec. II-C). */
-enum flbm_lattice { FLBM_D2Q9 = 0, FLBM_D3Q27 = 1 };
+/* Lattices: D2Q9 (Sec. II-B) and D3Q27 (Sec. II-C). FLBM_D3Q27_ISO is D3Q27 with its
+ * normal-stress modes 4-6 replaced by their trace and two deviators,
+ *   M4' = M4 + M5 + M6,  M5' = M4 - M5,  M6' = M4 + M5 - 2 M6   (norms 2/3, 4/9, 4/3),
+ * an orthogonal basis of the same space. The paper relaxes modes 4-6 at rate 1 (Sec. II-C),
+ * which makes the viscosity of extensional flow differ from that of shear; with the
+ * deviators at the shear rate (Lambda_5 = Lambda_6 = Lambda_7..9) the variant has one
+ * viscosity, and Lambda_4 is the bulk rate. Statistics report k_4..k_6 in this basis.
+ * Step variants 3, 4 and 6 run as 2, 2 and 5 for it. Not available in batches. */
+enum flbm_lattice { FLBM_D2Q9 = 0, FLBM_D3Q27 = 1, FLBM_D3Q27_ISO = 2 };
 
 /* Storage of the deviations d_i = f_i - w_i * rho0 in device memory. All moment
  * arithmetic is FP32 whatever the storage; statistics accumulate in FP64. */
@@ -74,7 +81,7 @@ size_t flbm_required_bytes(int lattice, const int64_t dims[3], int storage);
 
 /*
  * flbm_create - build a context for one periodic lattice at rest (f = f^eq(rho0, 0)).
- *   lattice : FLBM_D2Q9 or FLBM_D3Q27.
+ *   lattice : FLBM_D2Q9, FLBM_D3Q27 or FLBM_D3Q27_ISO.
  *   dims    : {nx, ny, nz}, each >= 1; nz must be 1 for D2Q9; ny, nz <= 65535;
  *             nx * ny * nz < 2^32 (the site index keys the noise).
  *   lambda  : Q relaxation rates Lambda_v (Eq. cm_collision) in the paper's mode order;

@@ -45,6 +45,7 @@ struct flbm_ctx {
   size_t sites_cap = 0;
   int variant = 0;  // enum StepVariant; 0 = default choice
   bool shear = false;  // rates follow the paper's structure (collide.cuh, SHEAR)
+  bool iso = false;    // the isotropic D3Q27 variant (lattice FLBM_D3Q27_ISO)
   int *d_status = nullptr;  // device status word of the pipelined kernel
   StepArgs args{};
   flbm_batch *owner = nullptr;  // set for a lattice of a batch (borrowed handle)
@@ -88,12 +89,13 @@ struct DeviceGuard {
   }
 };
 
-int q_of(int lattice) { return lattice == FLBM_D3Q27 ? 27 : 9; }
-int d_of(int lattice) { return lattice == FLBM_D3Q27 ? 3 : 2; }
+int q_of(int lattice) { return lattice == FLBM_D2Q9 ? 9 : 27; }
+int d_of(int lattice) { return lattice == FLBM_D2Q9 ? 2 : 3; }
 
 int check_geometry(int lattice, const int64_t dims[3], int storage) {
-  if (lattice != FLBM_D2Q9 && lattice != FLBM_D3Q27)
-    return fail(FLBM_EINVAL, "lattice must be FLBM_D2Q9 (0) or FLBM_D3Q27 (1), got %d", lattice);
+  if (lattice != FLBM_D2Q9 && lattice != FLBM_D3Q27 && lattice != FLBM_D3Q27_ISO)
+    return fail(FLBM_EINVAL, "lattice must be FLBM_D2Q9 (0), FLBM_D3Q27 (1) or FLBM_D3Q27_ISO (2), got %d",
+                lattice);
   if (!dims) return fail(FLBM_EINVAL, "dims is NULL");
   for (int a = 0; a < 3; ++a)
     if (dims[a] < 1) return fail(FLBM_EINVAL, "dims[%d] = %lld must be >= 1", a, (long long)dims[a]);
@@ -144,12 +146,14 @@ void fill_args(flbm_ctx *c) {
   for (int v = c->D + 1; v < c->Q; ++v) {
     const double L = c->lambda[v];
     a.om[v] = float(1.0 - L);
-    a.phc[v] = float(std::sqrt(c->kBT * L * (2.0 - L) * mode_bnorm(c->D, v) * 3.0));
+    a.phc[v] = float(std::sqrt(c->kBT * L * (2.0 - L) * mode_bnorm_lattice(c->lattice, v) * 3.0));
   }
-  // The paper's structure: rate 1 for every non-conserved mode except the shear modes.
+  // The paper's structure: rate 1 for every non-conserved mode except the shear modes
+  // (isotropic variant: except the second-order modes 4-9).
+  c->iso = c->lattice == FLBM_D3Q27_ISO;
   c->shear = true;
   for (int v = c->D + 1; v < c->Q; ++v) {
-    const bool is_shear = (c->D == 3) ? (v >= 7 && v <= 9) : (v == 4 || v == 5);
+    const bool is_shear = c->iso ? (v <= 9) : (c->D == 3) ? (v >= 7 && v <= 9) : (v == 4 || v == 5);
     if (!is_shear && c->lambda[v] != 1.0) c->shear = false;
   }
 }
@@ -229,7 +233,7 @@ void fill_stats(const flbm_ctx *c, const double *acc, int64_t step, flbm_stats_t
 
 int enqueue_stats(flbm_ctx *c, double *acc_dev) {
   FLBM_CUDA(cudaMemsetAsync(acc_dev, 0, sizeof(double) * stats_record_len(c->Q), c->stream));
-  FLBM_CUDA(launch_stats(c->D, c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
+  FLBM_CUDA(launch_stats(c->D, c->storage, c->iso, int(c->step & 1), c->f, c->N, int(c->dims[0]),
                          int(c->dims[1]), int(c->dims[2]), float(c->rho0), acc_dev, c->stream));
   return FLBM_OK;
 }
@@ -242,6 +246,10 @@ int resolve_variant(const flbm_ctx *c) {
   int v = c->variant;
   if (v == kStepAuto) v = kStepPair;
   if (v == kStepPipelined && !pipe) v = kStepPair;
+  if (c->iso) {  // the isotropic variant has the unrolled two-site kernels only
+    if (v == kStepPairRolled || v == kStepPipelined) v = kStepPair;
+    if (v == kStepPairRolledOcc) v = kStepPairOcc;
+  }
   if (v != kStepOneSite && c->dims[0] % 2 != 0) v = kStepOneSite;
   return v;
 }
@@ -397,7 +405,7 @@ int flbm_step(flbm_ctx *c, int64_t n) {
   for (int64_t s = 0; s < n; ++s) {
     c->args.step_lo = uint32_t(uint64_t(c->step));
     c->args.step_hi = uint32_t(uint64_t(c->step) >> 32);
-    FLBM_CUDA(launch_step(c->D, c->storage, resolve_variant(c), int(c->step & 1), noise, c->shear,
+    FLBM_CUDA(launch_step(c->D, c->storage, resolve_variant(c), int(c->step & 1), noise, c->shear, c->iso,
                           c->args, c->stream));
     ++c->step;
   }
@@ -668,6 +676,7 @@ int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
                                kStepPairRolledOcc};
     for (int v : candidates) {
       if ((v == kStepPairOcc || v == kStepPairRolledOcc) && c->D != 3) continue;  // same as 2 and 3
+      if (c->iso && (v == kStepPairRolled || v == kStepPipelined || v == kStepPairRolledOcc)) continue;
       if (v != kStepOneSite && c->dims[0] % 2 != 0) continue;
       if (v == kStepPipelined && !pipe_applicable(c->D, c->storage, int(c->dims[0]))) continue;
       c->variant = v;
@@ -926,6 +935,8 @@ int flbm_batch_create(flbm_batch **out, const flbm_lattice_spec *specs, int n, v
   for (int i = 0; i < n; ++i) {
     const flbm_lattice_spec &s = specs[i];
     if (s.reserved != 0) return fail(FLBM_EINVAL, "specs[%d].reserved must be 0", i);
+    if (s.lattice == FLBM_D3Q27_ISO)
+      return fail(FLBM_EINVAL, "specs[%d]: the isotropic D3Q27 variant is not available in batches", i);
     int st = check_geometry(s.lattice, s.dims, FLBM_FP32);
     if (st == FLBM_OK) st = check_params(s.lattice, s.lambda, s.kBT, s.rho0);
     if (st != FLBM_OK) return fail(st, "specs[%d]: %s", i, g_last_error.c_str());
@@ -1237,7 +1248,8 @@ extern "C" int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storag
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const long long N = (long long)(dims[0] * dims[1] * dims[2]);
   FLBM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * size_t(len), s));
-  FLBM_CUDA(launch_stats(d_of(lattice), storage, parity, dev_populations, N, int(dims[0]), int(dims[1]),
+  FLBM_CUDA(launch_stats(d_of(lattice), storage, lattice == FLBM_D3Q27_ISO, parity, dev_populations, N,
+                         int(dims[0]), int(dims[1]),
                          int(dims[2]), float(rho0), acc, s));
   double h[FLBM_NOALLOC_SCRATCH_DOUBLES];
   FLBM_CUDA(cudaMemcpyAsync(h, acc, sizeof(double) * size_t(len), cudaMemcpyDeviceToHost, s));

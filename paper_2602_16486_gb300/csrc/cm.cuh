@@ -397,4 +397,29 @@ __device__ __forceinline__ void site_central_moments(T (&F)[3][3][3], float rho0
   tile_shift_fwd<D>(F, vmul(m1, ux), vmul(m1, uy), vmul(m1, uz));
 }
 
+// ---- the isotropic D3Q27 variant ----------------------------------------------------------
+// Modes 4-6 of the variant are the trace and two deviators of the normal-stress modes of
+// Sec. II-C: M4' = M4 + M5 + M6, M5' = M4 - M5, M6' = M4 + M5 - 2 M6 (mutually orthogonal,
+// norms 2/3, 4/9, 4/3). These map the three values in place.
+template <typename T>
+__device__ __forceinline__ void iso_rotate(T &a, T &b, T &c) {  // (k4, k5, k6) -> (M4', M5', M6')
+  const T s = vadd(a, b);
+  const T d1 = vsub(a, b);
+  const T d2 = vfma(splat<T>(-2.0f), c, s);
+  a = vadd(s, c);
+  b = d1;
+  c = d2;
+}
+template <typename T>
+__device__ __forceinline__ void iso_unrotate(T &a, T &b, T &c) {  // (M4', M5', M6') -> (k4, k5, k6)
+  const T third = splat<T>(1.0f / 3.0f), half = splat<T>(0.5f);
+  const T s = vmul(third, vfma(splat<T>(2.0f), a, c));  // k4 + k5 = (2 M4' + M6') / 3
+  const T k6 = vmul(third, vsub(a, c));                 // (M4' - M6') / 3
+  const T k4 = vmul(half, vadd(s, b));
+  const T k5 = vmul(half, vsub(s, b));
+  a = k4;
+  b = k5;
+  c = k6;
+}
+
 }  // namespace flbm

@@ -80,10 +80,20 @@ __device__ __forceinline__ void add_noise_block(T (&F)[3][3][3], const R &rates,
 // and II-B). Then k*_v = phi_v eta_v needs no pre-collision value, and only the shear
 // central moments are formed, directly as k_ab = r_ab - rho u_a u_b (Sec. II-C prints
 // k7-k9 in this form) instead of through the full velocity shift.
-template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false, typename R, typename K>
+//
+// ISO (D3Q27 only): the isotropic variant, whose modes 4-6 are the trace and two deviators
+// of the normal stresses, M4' = M4 + M5 + M6, M5' = M4 - M5, M6' = M4 + M5 - 2 M6 (the
+// reading that gives one viscosity for every shear direction). The three tensor slots of
+// modes 4-6 hold (M4', M5', M6') while the modes are relaxed and the noise is added, and
+// are rotated back before the inverse transform. With SHEAR and ISO every non-conserved
+// mode but 4-9 relaxes at rate 1; modes 4-9 are formed directly from the raw second
+// moments: k_aa = P_aa - rho u_a^2, k_ab = P_ab - rho u_a u_b.
+template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false, bool ISO = false, typename R,
+          typename K>
 __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const R &rates, uint32_t site0,
                                               uint32_t step_lo, uint32_t step_hi, const K &keys,
                                               uint32_t dsite = 1) {
+  static_assert(!ISO || D == 3, "the isotropic variant is a D3Q27 basis");
   T drho, rho, ux, uy, uz;
   if (SHEAR) {
     site_macros<D>(F, rho0, drho, rho, ux, uy, uz);
@@ -97,11 +107,18 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
   if (D == 3) {
     if (SHEAR) {
       // raw (1,1,0), (1,0,1), (0,1,1) -> central; every other non-conserved mode restarts
-      // from k^eq = 0.
+      // from k^eq = 0 (ISO: also the normal stresses, rotated).
       const T nrho = vmul(splat<T>(-1.0f), rho);
       const T kxy = vfma(vmul(nrho, ux), uy, F[0][1][1]);
       const T kxz = vfma(vmul(nrho, ux), uz, F[1][0][1]);
       const T kyz = vfma(vmul(nrho, uy), uz, F[1][1][0]);
+      T kxx, kyy, kzz;
+      if (ISO) {
+        kxx = vfma(vmul(nrho, ux), ux, F[0][0][2]);
+        kyy = vfma(vmul(nrho, uy), uy, F[0][2][0]);
+        kzz = vfma(vmul(nrho, uz), uz, F[2][0][0]);
+        iso_rotate(kxx, kyy, kzz);
+      }
 #pragma unroll
       for (int v = 4; v < 27; ++v) {
         const int t = d3q27_mode_tensor(v);
@@ -110,7 +127,13 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
       F[0][1][1] = vmul(splat<T>(rates.om(7)), kxy);
       F[1][0][1] = vmul(splat<T>(rates.om(8)), kxz);
       F[1][1][0] = vmul(splat<T>(rates.om(9)), kyz);
+      if (ISO) {
+        F[0][0][2] = vmul(splat<T>(rates.om(4)), kxx);
+        F[0][2][0] = vmul(splat<T>(rates.om(5)), kyy);
+        F[2][0][0] = vmul(splat<T>(rates.om(6)), kzz);
+      }
     } else {
+      if (ISO) iso_rotate(F[0][0][2], F[0][2][0], F[2][0][0]);
 #pragma unroll
       for (int v = 4; v < 27; ++v) {
         const int t = d3q27_mode_tensor(v);
@@ -147,6 +170,7 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
         }
       }
     }
+    if (ISO) iso_unrotate(F[0][0][2], F[0][2][0], F[2][0][0]);
     F[0][0][1] = splat<T>(0.0f);  // k*_1 (x momentum, central)
     F[0][1][0] = splat<T>(0.0f);  // k*_2
     F[1][0][0] = splat<T>(0.0f);  // k*_3
@@ -198,12 +222,12 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
 }
 
 // The collision with per-mode arrays om_v, phc_v (kernel arguments).
-template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false>
+template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false, bool ISO = false>
 __device__ __forceinline__ void collide_tile(T (&F)[3][3][3], float rho0, const float *om,
                                              const float *phc, uint32_t site0, uint32_t step_lo,
                                              uint32_t step_hi, const uint32_t *ks0,
                                              const uint32_t *ks1) {
-  collide_rates<D, NOISE, T, ROLLED, SHEAR>(F, rho0, ArrayRates{om, phc}, site0, step_lo, step_hi,
+  collide_rates<D, NOISE, T, ROLLED, SHEAR, ISO>(F, rho0, ArrayRates{om, phc}, site0, step_lo, step_hi,
                                             KeyTable{ks0, ks1});
 }
 

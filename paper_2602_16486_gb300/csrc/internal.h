@@ -94,11 +94,16 @@ enum StepVariant {
   kStepVariantMax = 6
 };
 bool pipe_applicable(int D, int storage, int nx);
-cudaError_t launch_step(int D, int storage, int variant, int parity, bool noise, bool shear,
+cudaError_t launch_step(int D, int storage, int variant, int parity, bool noise, bool shear, bool iso,
                         const StepArgs &a, cudaStream_t s);
+// Per translation unit (step_16.cu, step_iso.cu).
+cudaError_t launch_step_16(int D, int storage, int variant, int parity, bool noise, bool shear, const StepArgs &a,
+                           cudaStream_t s);
+cudaError_t launch_step_iso(int storage, int variant, int parity, bool noise, bool shear, const StepArgs &a,
+                            cudaStream_t s);
 cudaError_t launch_step_pipelined(int D, int storage, int parity, bool noise, bool shear,
                                   const StepArgs &a, cudaStream_t s);
-cudaError_t launch_stats(int D, int storage, int parity, const void *f, long long plane, int nx,
+cudaError_t launch_stats(int D, int storage, bool iso, int parity, const void *f, long long plane, int nx,
                          int ny, int nz, float rho0, double *acc, cudaStream_t s);
 cudaError_t launch_init(int D, int storage, void *f, long long plane, int nx, int ny, int nz,
                         double rho0, double ux, double uy, double uz, double amp,
@@ -116,6 +121,8 @@ cudaError_t launch_gather_sites(int D, int storage, int parity, const void *f, l
 // Modal norms b_v of the device bases (host copy, computed from the same tensor
 // structure the kernels use) and the storage element size.
 double mode_bnorm(int D, int v);
+// b_v of the lattice's basis (lattice 2: the isotropic D3Q27 variant, modes 4-6 rotated).
+double mode_bnorm_lattice(int lattice, int v);
 size_t storage_bytes(int storage);
 
 }  // namespace flbm

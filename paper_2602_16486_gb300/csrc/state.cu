@@ -179,6 +179,11 @@ cudaError_t launch_gather_sites(int D, int storage, int parity, const void *f, l
 
 // b_v of the device bases: product of the 1-D norms (1, 1/3, 2/9) over the tensor
 // orders of mode v; the rotated D2Q9 pair 3, 4 has norm 2 * (2/9).
+double mode_bnorm_lattice(int lattice, int v) {
+  if (lattice == 2 && v >= 4 && v <= 6) return v == 4 ? 2.0 / 3.0 : (v == 5 ? 4.0 / 9.0 : 4.0 / 3.0);
+  return mode_bnorm(lattice == 0 ? 2 : 3, v);
+}
+
 double mode_bnorm(int D, int v) {
   const double b1[3] = {1.0, 1.0 / 3.0, 2.0 / 9.0};
   if (D == 3) {

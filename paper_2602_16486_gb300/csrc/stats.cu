@@ -50,7 +50,6 @@ int stats_nacc(int Q) { return Q == 27 ? StatsPlan<3>::NREC : StatsPlan<2>::NREC
 namespace {
 
 constexpr int kTileSites = 2 * kStatsBlock;  // 128 threads x 2 sites
-constexpr int kWarps = kStatsBlock / 32;
 constexpr int kFlushTiles = 8;
 
 template <int D>
@@ -88,7 +87,7 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 
 // Columns of the two sites of a pair (lane x: site s, lane y: site s + 1). PAIRROW: nx is
 // even, so s (even) and s + 1 share a row and load as pairs (cm.cuh, load_logical2).
-template <int D, typename S, int PARITY, bool PAIRROW>
+template <int D, typename S, int PARITY, bool PAIRROW, bool ISO>
 __device__ __forceinline__ void pair_columns(const S *__restrict__ f, long long plane, int nx, int ny, int nz,
                                              float rho0, long long s, long long N, float2 *col,
                                              unsigned &nonfinite) {
@@ -139,6 +138,7 @@ __device__ __forceinline__ void pair_columns(const S *__restrict__ f, long long 
     k[3] = vadd(F[1][0][2], F[1][2][0]);
     k[4] = vsub(F[1][0][2], F[1][2][0]);
   }
+  if (ISO) iso_rotate(k[4], k[5], k[6]);  // the isotropic variant's modes 4-6
   col[0] = make_float2(valid[0] ? 1.0f : 0.0f, valid[1] ? 1.0f : 0.0f);
   col[1] = drho;
   col[2] = vmul(rho, ux);
@@ -165,7 +165,7 @@ __device__ __forceinline__ void pair_columns(const S *__restrict__ f, long long 
   }
 }
 
-template <int D, typename S, int PARITY, bool PAIRROW>
+template <int D, typename S, int PARITY, bool PAIRROW, bool ISO>
 __global__ void __launch_bounds__(kStatsBlock, 3) stats_kernel(const S *__restrict__ f, long long plane,
                                                                int nx, int ny, int nz, float rho0,
                                                                double *__restrict__ acc) {
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kStatsBlock, 3) stats_kernel(const S *__restri
       float2 col[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) col[c] = make_float2(0.0f, 0.0f);
-      pair_columns<D, S, PARITY, PAIRROW>(f, plane, nx, ny, nz, rho0, base + 2 * threadIdx.x, N, col,
+      pair_columns<D, S, PARITY, PAIRROW, ISO>(f, plane, nx, ny, nz, rho0, base + 2 * threadIdx.x, N, col,
                                           nonfinite);
       // The two sites go to rows tid and tid + 128 (the sums do not depend on the order).
       const int r0 = threadIdx.x, r1 = threadIdx.x + kStatsBlock;
@@ -333,10 +333,10 @@ cudaError_t stats_grid(K kernel, size_t smem, long long tiles, int *grid) {
   return cudaSuccess;
 }
 
-template <int D, typename S, int PARITY, bool PAIRROW>
+template <int D, typename S, int PARITY, bool PAIRROW, bool ISO>
 cudaError_t launch_one(const S *p, long long plane, int nx, int ny, int nz, float rho0, double *acc,
                        cudaStream_t s) {
-  auto kernel = stats_kernel<D, S, PARITY, PAIRROW>;
+  auto kernel = stats_kernel<D, S, PARITY, PAIRROW, ISO>;
   const size_t smem = stats_smem<D, S>();
   const long long tiles = (plane + kTileSites - 1) / kTileSites;
   int grid = 0;
@@ -346,32 +346,38 @@ cudaError_t launch_one(const S *p, long long plane, int nx, int ny, int nz, floa
   return cudaGetLastError();
 }
 
-template <int D, typename S>
+template <int D, typename S, bool ISO>
 cudaError_t launch_typed(int parity, const void *f, long long plane, int nx, int ny, int nz,
                          float rho0, double *acc, cudaStream_t s) {
   const S *p = static_cast<const S *>(f);
   const bool pairrow = nx % 2 == 0;
   if (parity == 0)
-    return pairrow ? launch_one<D, S, 0, true>(p, plane, nx, ny, nz, rho0, acc, s)
-                   : launch_one<D, S, 0, false>(p, plane, nx, ny, nz, rho0, acc, s);
-  return pairrow ? launch_one<D, S, 1, true>(p, plane, nx, ny, nz, rho0, acc, s)
-                 : launch_one<D, S, 1, false>(p, plane, nx, ny, nz, rho0, acc, s);
+    return pairrow ? launch_one<D, S, 0, true, ISO>(p, plane, nx, ny, nz, rho0, acc, s)
+                   : launch_one<D, S, 0, false, ISO>(p, plane, nx, ny, nz, rho0, acc, s);
+  return pairrow ? launch_one<D, S, 1, true, ISO>(p, plane, nx, ny, nz, rho0, acc, s)
+                 : launch_one<D, S, 1, false, ISO>(p, plane, nx, ny, nz, rho0, acc, s);
 }
 
 }  // namespace
 
-cudaError_t launch_stats(int D, int storage, int parity, const void *f, long long plane, int nx,
+cudaError_t launch_stats(int D, int storage, bool iso, int parity, const void *f, long long plane, int nx,
                          int ny, int nz, float rho0, double *acc, cudaStream_t s) {
-  if (D == 3) {
-    if (storage == 0) return launch_typed<3, float>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+  if (D == 3 && iso) {
+    if (storage == 0) return launch_typed<3, float, true>(parity, f, plane, nx, ny, nz, rho0, acc, s);
     if (storage == 1)
-      return launch_typed<3, __nv_bfloat16>(parity, f, plane, nx, ny, nz, rho0, acc, s);
-    return launch_typed<3, __half>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+      return launch_typed<3, __nv_bfloat16, true>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+    return launch_typed<3, __half, true>(parity, f, plane, nx, ny, nz, rho0, acc, s);
   }
-  if (storage == 0) return launch_typed<2, float>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+  if (D == 3) {
+    if (storage == 0) return launch_typed<3, float, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+    if (storage == 1)
+      return launch_typed<3, __nv_bfloat16, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+    return launch_typed<3, __half, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+  }
+  if (storage == 0) return launch_typed<2, float, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
   if (storage == 1)
-    return launch_typed<2, __nv_bfloat16>(parity, f, plane, nx, ny, nz, rho0, acc, s);
-  return launch_typed<2, __half>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+    return launch_typed<2, __nv_bfloat16, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+  return launch_typed<2, __half, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
 }
 
 }  // namespace flbm

@@ -1,0 +1,102 @@
+// Kernel templates of the fused step (documented in step.cu), shared by the translation
+// units that instantiate them: step.cu (FP32 storage and the dispatch), step_16.cu
+// (BF16 and FP16 storage) and step_iso.cu (the isotropic D3Q27 variant).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "collide.cuh"
+#include "internal.h"
+
+namespace flbm {
+namespace {
+
+template <int D, typename S, int PARITY, bool NOISE, bool SHEAR, bool ISO>
+__global__ void __launch_bounds__(kStepBlock) step_kernel(const StepArgs a) {
+  const int x = blockIdx.x * kStepBlock + threadIdx.x;
+  if (x >= a.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const Neighbourhood nb = neighbourhood(x, y, z, a.nx, a.ny, a.nz);
+  S *__restrict__ f = static_cast<S *>(a.f);
+
+  float F[3][3][3];
+  load_logical<D, S, PARITY>(f, a.plane, nb, F);
+  const uint32_t site = (uint32_t)(x + (long long)a.nx * (y + (long long)a.ny * z));
+  collide_tile<D, NOISE, float, false, SHEAR, ISO>(F, a.rho0, a.om, a.phc, site, a.step_lo, a.step_hi, a.ks0,
+                                                   a.ks1);
+  store_streamed<D, S, PARITY>(f, a.plane, nb, F);
+}
+
+template <int D, typename S, int PARITY, bool NOISE, bool ROLLED, bool SHEAR, int MINB, bool ISO>
+__global__ void __launch_bounds__(kStepBlock, MINB) step2_kernel(const StepArgs a) {
+  const int x0 = 2 * (blockIdx.x * kStepBlock + threadIdx.x);
+  if (x0 >= a.nx) return;
+  const Addr2 ad = addr2(x0, blockIdx.y, blockIdx.z, a.nx, a.ny, a.nz);
+  S *__restrict__ f = static_cast<S *>(a.f);
+
+  float2 F[3][3][3];
+  load_logical2<D, S, PARITY>(f, a.plane, ad, F);
+  collide_tile<D, NOISE, float2, ROLLED, SHEAR, ISO>(F, a.rho0, a.om, a.phc, (uint32_t)ad.s0, a.step_lo,
+                                                     a.step_hi, a.ks0, a.ks1);
+  store_streamed2<D, S, PARITY>(f, a.plane, ad, F);
+}
+
+template <typename S>
+constexpr int storage_code() {
+  return sizeof(S) == 4 ? 0 : (std::is_same<S, __nv_bfloat16>::value ? 1 : 2);
+}
+
+// One launch of variant 1, 2, 3, 5 or 6 (the pipelined variant 4 lives in
+// step_pipe.cu). ISO kernels exist for variants 1, 2 and 5 only; the host maps 3 and 6
+// to 2 and 5 for them.
+template <int D, typename S, int PARITY, bool NOISE, bool SHEAR, bool ISO>
+cudaError_t launch_kernel(int variant, const StepArgs &a, cudaStream_t s) {
+  const dim3 block(kStepBlock);
+  if (variant != kStepOneSite) {
+    // Register caps: 128 (four blocks of 128 threads per SM) or, for D3Q27, 102 (five
+    // blocks: more warps to hide latency, at the risk of spills). D2Q9 needs fewer than
+    // 102 registers either way, so its variants 5 and 6 are 2 and 3.
+    constexpr int kOcc = D == 3 ? 5 : 4;
+    const dim3 grid((a.nx / 2 + kStepBlock - 1) / kStepBlock, a.ny, a.nz);
+    const bool occ = variant == kStepPairOcc || variant == kStepPairRolledOcc;
+    const bool rolled = !ISO && (variant == kStepPairRolled || variant == kStepPairRolledOcc);
+    if (occ) {
+      if (rolled)
+        step2_kernel<D, S, PARITY, NOISE, !ISO, SHEAR, kOcc, ISO><<<grid, block, 0, s>>>(a);
+      else
+        step2_kernel<D, S, PARITY, NOISE, false, SHEAR, kOcc, ISO><<<grid, block, 0, s>>>(a);
+    } else {
+      if (rolled)
+        step2_kernel<D, S, PARITY, NOISE, !ISO, SHEAR, 4, ISO><<<grid, block, 0, s>>>(a);
+      else
+        step2_kernel<D, S, PARITY, NOISE, false, SHEAR, 4, ISO><<<grid, block, 0, s>>>(a);
+    }
+  } else {
+    const dim3 grid((a.nx + kStepBlock - 1) / kStepBlock, a.ny, a.nz);
+    step_kernel<D, S, PARITY, NOISE, SHEAR, ISO><<<grid, block, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <int D, typename S, bool ISO>
+cudaError_t launch_typed(int variant, int parity, bool noise, bool shear, const StepArgs &a, cudaStream_t s) {
+  if (!ISO && variant == kStepPipelined)
+    return launch_step_pipelined(D, storage_code<S>(), parity, noise, shear, a, s);
+  if (parity == 0) {
+    if (noise)
+      return shear ? launch_kernel<D, S, 0, true, true, ISO>(variant, a, s)
+                   : launch_kernel<D, S, 0, true, false, ISO>(variant, a, s);
+    return shear ? launch_kernel<D, S, 0, false, true, ISO>(variant, a, s)
+                 : launch_kernel<D, S, 0, false, false, ISO>(variant, a, s);
+  }
+  if (noise)
+    return shear ? launch_kernel<D, S, 1, true, true, ISO>(variant, a, s)
+                 : launch_kernel<D, S, 1, true, false, ISO>(variant, a, s);
+  return shear ? launch_kernel<D, S, 1, false, true, ISO>(variant, a, s)
+               : launch_kernel<D, S, 1, false, false, ISO>(variant, a, s);
+}
+
+}  // namespace
+}  // namespace flbm
