@@ -24,8 +24,9 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 D2Q9 = 0
 D3Q27 = 1
 D3Q27_ISO = 2  # D3Q27 with trace/deviator normal-stress modes (flbm_oracle.cpp)
-_Q = {D2Q9: 9, D3Q27: 27, D3Q27_ISO: 27}
-_D = {D2Q9: 2, D3Q27: 3, D3Q27_ISO: 3}
+D3Q19 = 3
+_Q = {D2Q9: 9, D3Q27: 27, D3Q27_ISO: 27, D3Q19: 19}
+_D = {D2Q9: 2, D3Q27: 3, D3Q27_ISO: 3, D3Q19: 3}
 
 _lib = None
 

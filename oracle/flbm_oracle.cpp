@@ -93,12 +93,29 @@ Lattice make_d3q27() {
   return L;
 }
 
+// D3Q19 (Sec. II-C, "Lattice-agnostic construction"): the rest velocity, the six axis
+// velocities and the twelve face diagonals, weights 1/3, 1/18, 1/36. The paper lists the
+// velocities by group only; they are taken in the order of the first 19 D3Q27 velocities.
+Lattice make_d3q19() {
+  const Lattice q27 = make_d3q27();
+  Lattice L{};
+  L.D = 3;
+  L.Q = 19;
+  for (int i = 0; i < 19; ++i)
+    for (int a = 0; a < 3; ++a) L.c[i][a] = q27.c[i][a];
+  L.w[0] = 1.0 / 3.0;
+  for (int i = 1; i <= 6; ++i) L.w[i] = 1.0 / 18.0;
+  for (int i = 7; i <= 18; ++i) L.w[i] = 1.0 / 36.0;
+  return L;
+}
+
 // Lattice ids: 0 D2Q9, 1 D3Q27, 2 D3Q27 with the isotropic normal-stress modes (same
-// velocities and weights as 1; see basis_d3q27_iso).
+// velocities and weights as 1; see basis_d3q27_iso), 3 D3Q19.
 const Lattice &lattice(int id) {
   static const Lattice d2q9 = make_d2q9();
   static const Lattice d3q27 = make_d3q27();
-  return id == 0 ? d2q9 : d3q27;
+  static const Lattice d3q19 = make_d3q19();
+  return id == 0 ? d2q9 : (id == 3 ? d3q19 : d3q27);
 }
 
 // ---------------------------------------------------------------------------
@@ -175,8 +192,37 @@ double basis_d3q27_iso(int v, double x, double y, double z) {
   return basis_d3q27(v, x, y, z);
 }
 
+// D3Q19 orthogonal basis as printed in Sec. II-C ("Lattice-agnostic construction");
+// c2 = |c|^2.
+double basis_d3q19(int v, double x, double y, double z) {
+  const double c2 = x * x + y * y + z * z;
+  switch (v) {
+    case 0: return 1.0;
+    case 1: return x;
+    case 2: return y;
+    case 3: return z;
+    case 4: return c2 - 1.0;
+    case 5: return 3.0 * x * x - c2;
+    case 6: return y * y - z * z;
+    case 7: return x * y;
+    case 8: return y * z;
+    case 9: return x * z;
+    case 10: return x * (3.0 * c2 - 5.0);
+    case 11: return y * (3.0 * c2 - 5.0);
+    case 12: return z * (3.0 * c2 - 5.0);
+    case 13: return x * (y * y - z * z);
+    case 14: return y * (z * z - x * x);
+    case 15: return z * (x * x - y * y);
+    case 16: return 3.0 * c2 * c2 - 6.0 * c2 + 1.0;
+    case 17: return (2.0 * c2 - 3.0) * (3.0 * x * x - c2);
+    case 18: return (2.0 * c2 - 3.0) * (y * y - z * z);
+  }
+  return 0.0;
+}
+
 double basis(int lat, int v, const double cbar[3]) {
   if (lat == 0) return basis_d2q9(v, cbar[0], cbar[1]);
+  if (lat == 3) return basis_d3q19(v, cbar[0], cbar[1], cbar[2]);
   if (lat == 2) return basis_d3q27_iso(v, cbar[0], cbar[1], cbar[2]);
   return basis_d3q27(v, cbar[0], cbar[1], cbar[2]);
 }
@@ -269,6 +315,21 @@ double H(const int *c, const char *s) {
 // (sixth-order expansion).
 void feq(int lat, double rho, const double u[3], double *f) {
   const Lattice &L = lattice(lat);
+  if (lat == 3) {
+    // D3Q19: the printed fourth-order populations do not conserve mass as transcribed
+    // (their sum is rho - 2 rho u^2 / 3 + O(u^4)). The equilibrium is taken as the one
+    // the paper states they project to: the populations whose central moments are
+    // k^eq = (rho, 0, ..., 0), f^eq = T(u)^{-1} k^eq.
+    std::vector<double> T;
+    build_T(lat, u, T);
+    std::vector<double> keq(size_t(L.Q), 0.0), x;
+    keq[0] = rho;
+    if (!lu_solve(L.Q, T, x, keq.data()))
+      for (int i = 0; i < L.Q; ++i) f[i] = NAN;
+    else
+      for (int i = 0; i < L.Q; ++i) f[i] = x[size_t(i)];
+    return;
+  }
   const double s2 = CS2, s4 = CS2 * CS2, s6 = s4 * CS2, s8 = s4 * s4, s10 = s8 * CS2,
                s12 = s6 * s6;
   const double ux = u[0], uy = u[1], uz = (lat == 0 ? 0.0 : u[2]);
