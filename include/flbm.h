@@ -40,8 +40,13 @@ typedef struct flbm_batch flbm_batch;
  * which makes the viscosity of extensional flow differ from that of shear; with the
  * deviators at the shear rate (Lambda_5 = Lambda_6 = Lambda_7..9) the variant has one
  * viscosity, and Lambda_4 is the bulk rate. Statistics report k_4..k_6 in this basis.
- * Step variants 3, 4 and 6 run as 2, 2 and 5 for it. Not available in batches. */
-enum flbm_lattice { FLBM_D2Q9 = 0, FLBM_D3Q27 = 1, FLBM_D3Q27_ISO = 2 };
+ * Step variants 3, 4 and 6 run as 2, 2 and 5 for it. Not available in batches.
+ * FLBM_D3Q19 is the reduced lattice of Sec. II-C ("Lattice-agnostic construction and the
+ * D3Q19 example"): rest, axis and face-diagonal velocities (weights 1/3, 1/18, 1/36) in the
+ * order of the first 19 D3Q27 velocities, the printed 19-mode basis and norms, Lambda_7..9
+ * the shear rates, and the equilibrium whose central moments are (rho, 0, ..., 0). Step
+ * variants 3, 4 and 6 run as 2, 2 and 5 for it. Not available in batches. */
+enum flbm_lattice { FLBM_D2Q9 = 0, FLBM_D3Q27 = 1, FLBM_D3Q27_ISO = 2, FLBM_D3Q19 = 3 };
 
 /* Storage of the deviations d_i = f_i - w_i * rho0 in device memory. All moment
  * arithmetic is FP32 whatever the storage; statistics accumulate in FP64. */
@@ -81,7 +86,7 @@ size_t flbm_required_bytes(int lattice, const int64_t dims[3], int storage);
 
 /*
  * flbm_create - build a context for one periodic lattice at rest (f = f^eq(rho0, 0)).
- *   lattice : FLBM_D2Q9, FLBM_D3Q27 or FLBM_D3Q27_ISO.
+ *   lattice : FLBM_D2Q9, FLBM_D3Q27, FLBM_D3Q27_ISO or FLBM_D3Q19.
  *   dims    : {nx, ny, nz}, each >= 1; nz must be 1 for D2Q9; ny, nz <= 65535;
  *             nx * ny * nz < 2^32 (the site index keys the noise).
  *   lambda  : Q relaxation rates Lambda_v (Eq. cm_collision) in the paper's mode order;

@@ -89,12 +89,18 @@ struct DeviceGuard {
   }
 };
 
-int q_of(int lattice) { return lattice == FLBM_D2Q9 ? 9 : 27; }
+int q_of(int lattice) { return lattice == FLBM_D2Q9 ? 9 : (lattice == FLBM_D3Q19 ? 19 : 27); }
 int d_of(int lattice) { return lattice == FLBM_D2Q9 ? 2 : 3; }
+// Lattice code of the state, exchange and statistics kernels: 2 (D2Q9), 3 (D3Q27, both
+// bases) or 19 (D3Q19).
+int klat(int lattice) { return lattice == FLBM_D2Q9 ? 2 : (lattice == FLBM_D3Q19 ? 19 : 3); }
+// Lattices whose step kernels exist for variants 1, 2 and 5 only.
+bool pair_variants_only(int lattice) { return lattice == FLBM_D3Q27_ISO || lattice == FLBM_D3Q19; }
 
 int check_geometry(int lattice, const int64_t dims[3], int storage) {
-  if (lattice != FLBM_D2Q9 && lattice != FLBM_D3Q27 && lattice != FLBM_D3Q27_ISO)
-    return fail(FLBM_EINVAL, "lattice must be FLBM_D2Q9 (0), FLBM_D3Q27 (1) or FLBM_D3Q27_ISO (2), got %d",
+  if (lattice != FLBM_D2Q9 && lattice != FLBM_D3Q27 && lattice != FLBM_D3Q27_ISO && lattice != FLBM_D3Q19)
+    return fail(FLBM_EINVAL,
+                "lattice must be FLBM_D2Q9 (0), FLBM_D3Q27 (1), FLBM_D3Q27_ISO (2) or FLBM_D3Q19 (3), got %d",
                 lattice);
   if (!dims) return fail(FLBM_EINVAL, "dims is NULL");
   for (int a = 0; a < 3; ++a)
@@ -233,7 +239,7 @@ void fill_stats(const flbm_ctx *c, const double *acc, int64_t step, flbm_stats_t
 
 int enqueue_stats(flbm_ctx *c, double *acc_dev) {
   FLBM_CUDA(cudaMemsetAsync(acc_dev, 0, sizeof(double) * stats_record_len(c->Q), c->stream));
-  FLBM_CUDA(launch_stats(c->D, c->storage, c->iso, int(c->step & 1), c->f, c->N, int(c->dims[0]),
+  FLBM_CUDA(launch_stats(klat(c->lattice), c->storage, c->iso, int(c->step & 1), c->f, c->N, int(c->dims[0]),
                          int(c->dims[1]), int(c->dims[2]), float(c->rho0), acc_dev, c->stream));
   return FLBM_OK;
 }
@@ -246,7 +252,7 @@ int resolve_variant(const flbm_ctx *c) {
   int v = c->variant;
   if (v == kStepAuto) v = kStepPair;
   if (v == kStepPipelined && !pipe) v = kStepPair;
-  if (c->iso) {  // the isotropic variant has the unrolled two-site kernels only
+  if (pair_variants_only(c->lattice)) {  // unrolled two-site kernels only
     if (v == kStepPairRolled || v == kStepPipelined) v = kStepPair;
     if (v == kStepPairRolledOcc) v = kStepPairOcc;
   }
@@ -389,7 +395,7 @@ int flbm_init_uniform(flbm_ctx *c, const double u0[3], double amp, uint64_t pert
   if (c->owner && c->step != 0)
     return fail(FLBM_ESTATE, "a lattice of a batch can be initialised only while the batch is at step 0");
   DeviceGuard g(c->device);
-  FLBM_CUDA(launch_init(c->D, c->storage, c->f, c->N, int(c->dims[0]), int(c->dims[1]),
+  FLBM_CUDA(launch_init(klat(c->lattice), c->storage, c->f, c->N, int(c->dims[0]), int(c->dims[1]),
                         int(c->dims[2]), c->rho0, u0[0], u0[1], c->D == 3 ? u0[2] : 0.0, amp,
                         perturb_seed, c->stream));
   c->step = 0;
@@ -405,7 +411,7 @@ int flbm_step(flbm_ctx *c, int64_t n) {
   for (int64_t s = 0; s < n; ++s) {
     c->args.step_lo = uint32_t(uint64_t(c->step));
     c->args.step_hi = uint32_t(uint64_t(c->step) >> 32);
-    FLBM_CUDA(launch_step(c->D, c->storage, resolve_variant(c), int(c->step & 1), noise, c->shear, c->iso,
+    FLBM_CUDA(launch_step(c->lattice, c->storage, resolve_variant(c), int(c->step & 1), noise, c->shear,
                           c->args, c->stream));
     ++c->step;
   }
@@ -501,7 +507,7 @@ int flbm_get_populations(flbm_ctx *c, double *host, size_t count) {
   int st = ensure_stage(c, size_t(c->N));
   if (st != FLBM_OK) return st;
   for (int q = 0; q < c->Q; ++q) {
-    FLBM_CUDA(launch_gather_plane(c->D, c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
+    FLBM_CUDA(launch_gather_plane(klat(c->lattice), c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
                                   int(c->dims[1]), int(c->dims[2]), c->rho0, q, c->d_stage, c->stream));
     FLBM_CUDA(cudaMemcpyAsync(host + size_t(q) * size_t(c->N), c->d_stage, sizeof(double) * size_t(c->N),
                               cudaMemcpyDeviceToHost, c->stream));
@@ -521,7 +527,7 @@ int flbm_set_populations(flbm_ctx *c, const double *host, size_t count) {
   for (int q = 0; q < c->Q; ++q) {
     FLBM_CUDA(cudaMemcpyAsync(c->d_stage, host + size_t(q) * size_t(c->N), sizeof(double) * size_t(c->N),
                               cudaMemcpyHostToDevice, c->stream));
-    FLBM_CUDA(launch_scatter_plane(c->D, c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
+    FLBM_CUDA(launch_scatter_plane(klat(c->lattice), c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
                                    int(c->dims[1]), int(c->dims[2]), c->rho0, q, c->d_stage, c->stream));
   }
   FLBM_CUDA(cudaStreamSynchronize(c->stream));
@@ -551,7 +557,7 @@ int flbm_get_sites(flbm_ctx *c, const int64_t *sites, size_t n, double *out) {
   if (st != FLBM_OK) return st;
   static_assert(sizeof(long long) == sizeof(int64_t), "site index width");
   FLBM_CUDA(cudaMemcpyAsync(c->d_sites, sites, n * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
-  FLBM_CUDA(launch_gather_sites(c->D, c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
+  FLBM_CUDA(launch_gather_sites(klat(c->lattice), c->storage, int(c->step & 1), c->f, c->N, int(c->dims[0]),
                                 int(c->dims[1]), int(c->dims[2]), c->rho0, c->d_sites, (long long)n,
                                 c->d_stage, c->stream));
   FLBM_CUDA(cudaMemcpyAsync(out, c->d_stage, n * size_t(c->Q) * sizeof(double), cudaMemcpyDeviceToHost,
@@ -676,7 +682,9 @@ int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
                                kStepPairRolledOcc};
     for (int v : candidates) {
       if ((v == kStepPairOcc || v == kStepPairRolledOcc) && c->D != 3) continue;  // same as 2 and 3
-      if (c->iso && (v == kStepPairRolled || v == kStepPipelined || v == kStepPairRolledOcc)) continue;
+      if (pair_variants_only(c->lattice) &&
+          (v == kStepPairRolled || v == kStepPipelined || v == kStepPairRolledOcc))
+        continue;
       if (v != kStepOneSite && c->dims[0] % 2 != 0) continue;
       if (v == kStepPipelined && !pipe_applicable(c->D, c->storage, int(c->dims[0]))) continue;
       c->variant = v;
@@ -935,8 +943,8 @@ int flbm_batch_create(flbm_batch **out, const flbm_lattice_spec *specs, int n, v
   for (int i = 0; i < n; ++i) {
     const flbm_lattice_spec &s = specs[i];
     if (s.reserved != 0) return fail(FLBM_EINVAL, "specs[%d].reserved must be 0", i);
-    if (s.lattice == FLBM_D3Q27_ISO)
-      return fail(FLBM_EINVAL, "specs[%d]: the isotropic D3Q27 variant is not available in batches", i);
+    if (s.lattice == FLBM_D3Q27_ISO || s.lattice == FLBM_D3Q19)
+      return fail(FLBM_EINVAL, "specs[%d]: only FLBM_D2Q9 and FLBM_D3Q27 lattices are available in batches", i);
     int st = check_geometry(s.lattice, s.dims, FLBM_FP32);
     if (st == FLBM_OK) st = check_params(s.lattice, s.lambda, s.kBT, s.rho0);
     if (st != FLBM_OK) return fail(st, "specs[%d]: %s", i, g_last_error.c_str());
@@ -1248,7 +1256,7 @@ extern "C" int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storag
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const long long N = (long long)(dims[0] * dims[1] * dims[2]);
   FLBM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * size_t(len), s));
-  FLBM_CUDA(launch_stats(d_of(lattice), storage, lattice == FLBM_D3Q27_ISO, parity, dev_populations, N,
+  FLBM_CUDA(launch_stats(klat(lattice), storage, lattice == FLBM_D3Q27_ISO, parity, dev_populations, N,
                          int(dims[0]), int(dims[1]),
                          int(dims[2]), float(rho0), acc, s));
   double h[FLBM_NOALLOC_SCRATCH_DOUBLES];

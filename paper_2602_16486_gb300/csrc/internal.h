@@ -94,13 +94,16 @@ enum StepVariant {
   kStepVariantMax = 6
 };
 bool pipe_applicable(int D, int storage, int nx);
-cudaError_t launch_step(int D, int storage, int variant, int parity, bool noise, bool shear, bool iso,
+// lattice: the public lattice id (0 D2Q9, 1 D3Q27, 2 D3Q27 isotropic, 3 D3Q19).
+cudaError_t launch_step(int lattice, int storage, int variant, int parity, bool noise, bool shear,
                         const StepArgs &a, cudaStream_t s);
 // Per translation unit (step_16.cu, step_iso.cu).
 cudaError_t launch_step_16(int D, int storage, int variant, int parity, bool noise, bool shear, const StepArgs &a,
                            cudaStream_t s);
 cudaError_t launch_step_iso(int storage, int variant, int parity, bool noise, bool shear, const StepArgs &a,
                             cudaStream_t s);
+cudaError_t launch_step_d3q19(int storage, int variant, int parity, bool noise, bool shear, const StepArgs &a,
+                              cudaStream_t s);
 cudaError_t launch_step_pipelined(int D, int storage, int parity, bool noise, bool shear,
                                   const StepArgs &a, cudaStream_t s);
 cudaError_t launch_stats(int D, int storage, bool iso, int parity, const void *f, long long plane, int nx,

@@ -1,5 +1,5 @@
-// Device-side lattice tables for the fused step: D2Q9 (Sec. II-B) and D3Q27 (Sec. II-C)
-// in the paper's velocity order, written as constexpr index functions so that every
+// Device-side lattice tables for the fused step: D2Q9 (Sec. II-B), D3Q27 (Sec. II-C) and
+// D3Q19 (Sec. II-C example) in the paper's velocity order, written as constexpr index functions so that every
 // table lookup in an unrolled loop folds to a constant.
 //
 // Moment bookkeeping. Both orthogonal bases are (up to a rotation of two D2Q9 modes)
@@ -85,6 +85,19 @@ struct Lat<3> {
   }
 };
 
+// D3Q19 (Sec. II-C, "Lattice-agnostic construction and the D3Q19 example"): the rest
+// velocity, the six axes and the twelve face diagonals, i.e. the first 19 velocities of
+// the D3Q27 order. Kernels that address populations by velocity take the lattice code 19.
+template <>
+struct Lat<19> {
+  static constexpr int D = 3;
+  static constexpr int Q = 19;
+  __host__ __device__ static constexpr int index(int cx, int cy, int cz) { return Lat<3>::index(cx, cy, cz); }
+  __host__ __device__ static constexpr int cx(int i) { return Lat<3>::cx(i); }
+  __host__ __device__ static constexpr int cy(int i) { return Lat<3>::cy(i); }
+  __host__ __device__ static constexpr int cz(int i) { return Lat<3>::cz(i); }
+};
+
 template <int D>
 __host__ __device__ constexpr int opposite(int i) {
   return Lat<D>::index(-Lat<D>::cx(i), -Lat<D>::cy(i), -Lat<D>::cz(i));
@@ -95,7 +108,8 @@ __host__ __device__ constexpr double weight1d(int c) { return c == 0 ? 2.0 / 3.0
 
 template <int D>
 __host__ __device__ constexpr double weight(int i) {
-  return weight1d(Lat<D>::cx(i)) * weight1d(Lat<D>::cy(i)) * (D == 3 ? weight1d(Lat<D>::cz(i)) : 1.0);
+  return D == 19 ? (i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0))  // D3Q19: not a product
+                 : weight1d(Lat<D>::cx(i)) * weight1d(Lat<D>::cy(i)) * (D == 3 ? weight1d(Lat<D>::cz(i)) : 1.0);
 }
 
 // Tensor orders (a, b, c) of D3Q27 mode v (Sec. II-C basis, with M_15 = c_y^2 c_z - cs^2 c_z),

@@ -4,10 +4,13 @@
 // Equilibrium (Sec. II-B Eq. feq for D2Q9 to fourth order, Sec. II-C for D3Q27 to
 // sixth order): on these lattices the complete Hermite expansion equals the product
 //   f^eq_i = rho * prod_a g(c_ia, u_a),  g(0, u) = 2/3 - u^2,  g(+-1, u) = (1 +- 3u + 3u^2)/6,
-// which is what the initialiser evaluates (FP64, once per run).
+// which is what the initialiser evaluates (FP64, once per run). D3Q19 (lattice code 19)
+// has no product form; its equilibrium is the state with central moments (rho, 0, ..., 0),
+// built in FP64 with the generated transforms of d3q19_gen.cuh.
 #include <cuda_runtime.h>
 
 #include "cm.cuh"
+#include "d3q19_gen.cuh"
 #include "internal.h"
 #include "philox.cuh"
 
@@ -45,11 +48,27 @@ __global__ void init_kernel(S *__restrict__ f, long long plane, int nx, int ny, 
     rho = rho0 * (1.0 + amp * (2.0 * U - 1.0));
   }
   constexpr int Q = Lat<D>::Q;
+  if constexpr (D == 19) {
+    // r* from k^eq = (rho, 0, ...): rows 4..18 by the inverse shift, r*_0 = rho - rho0,
+    // r*_a = rho u_a; then the deviations M^{-1} r*.
+    double r[19], d[19];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    double fe = rho * g1d(Lat<D>::cx(i), ux) * g1d(Lat<D>::cy(i), uy);
-    if (D == 3) fe *= g1d(Lat<D>::cz(i), uz);
-    Storage<S>::store(f + (long long)i * plane + s, (float)(fe - weight<D>(i) * rho0));
+    for (int v = 0; v < 19; ++v) r[v] = 0.0;
+    d3q19_raw_from_central(r, rho, ux, uy, uz);
+    r[0] = rho - rho0;
+    r[1] = rho * ux;
+    r[2] = rho * uy;
+    r[3] = rho * uz;
+    d3q19_pop(r, d);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) Storage<S>::store(f + (long long)i * plane + s, (float)d[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      double fe = rho * g1d(Lat<D>::cx(i), ux) * g1d(Lat<D>::cy(i), uy);
+      if (D == 3) fe *= g1d(Lat<D>::cz(i), uz);
+      Storage<S>::store(f + (long long)i * plane + s, (float)(fe - weight<D>(i) * rho0));
+    }
   }
 }
 
@@ -98,7 +117,9 @@ cudaError_t init_typed(int D, void *f, long long plane, int nx, int ny, int nz, 
                        double ux, double uy, double uz, double amp, uint64_t seed, cudaStream_t s) {
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   S *p = static_cast<S *>(f);
-  if (D == 3)
+  if (D == 19)
+    init_kernel<19, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, ux, uy, uz, amp, k0, k1);
+  else if (D == 3)
     init_kernel<3, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, ux, uy, uz, amp, k0, k1);
   else
     init_kernel<2, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, ux, uy, 0.0, amp, k0, k1);
@@ -109,7 +130,9 @@ template <typename S>
 cudaError_t gather_typed(int D, int parity, const void *f, long long plane, int nx, int ny, int nz,
                          double rho0, int q, double *out, cudaStream_t s) {
   const S *p = static_cast<const S *>(f);
-  if (D == 3)
+  if (D == 19)
+    gather_plane_kernel<19, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, parity, q, out);
+  else if (D == 3)
     gather_plane_kernel<3, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, parity, q, out);
   else
     gather_plane_kernel<2, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, parity, q, out);
@@ -120,7 +143,9 @@ template <typename S>
 cudaError_t scatter_typed(int D, int parity, void *f, long long plane, int nx, int ny, int nz,
                           double rho0, int q, const double *in, cudaStream_t s) {
   S *p = static_cast<S *>(f);
-  if (D == 3)
+  if (D == 19)
+    scatter_plane_kernel<19, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, parity, q, in);
+  else if (D == 3)
     scatter_plane_kernel<3, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, parity, q, in);
   else
     scatter_plane_kernel<2, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, parity, q, in);
@@ -131,9 +156,11 @@ template <typename S>
 cudaError_t sites_typed(int D, int parity, const void *f, long long plane, int nx, int ny, int nz,
                         double rho0, const long long *sites, long long n, double *out, cudaStream_t s) {
   const S *p = static_cast<const S *>(f);
-  const int Q = D == 3 ? 27 : 9;
+  const int Q = D == 3 ? 27 : (D == 19 ? 19 : 9);
   if (n == 0) return cudaSuccess;
-  if (D == 3)
+  if (D == 19)
+    gather_sites_kernel<19, S><<<blocks_for(n * Q, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, parity, sites, n, out);
+  else if (D == 3)
     gather_sites_kernel<3, S><<<blocks_for(n * Q, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, parity, sites, n, out);
   else
     gather_sites_kernel<2, S><<<blocks_for(n * Q, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, parity, sites, n, out);
@@ -181,6 +208,12 @@ cudaError_t launch_gather_sites(int D, int storage, int parity, const void *f, l
 // orders of mode v; the rotated D2Q9 pair 3, 4 has norm 2 * (2/9).
 double mode_bnorm_lattice(int lattice, int v) {
   if (lattice == 2 && v >= 4 && v <= 6) return v == 4 ? 2.0 / 3.0 : (v == 5 ? 4.0 / 9.0 : 4.0 / 3.0);
+  if (lattice == 3) {  // D3Q19, printed in Sec. II-C
+    const double b[19] = {1.0,       1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, 4.0 / 3.0, 4.0 / 9.0,
+                          1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 9.0,
+                          2.0 / 9.0, 2.0 / 9.0, 2.0,       4.0 / 3.0, 4.0 / 9.0};
+    return b[v];
+  }
   return mode_bnorm(lattice == 0 ? 2 : 3, v);
 }
 

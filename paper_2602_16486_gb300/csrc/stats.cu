@@ -29,6 +29,7 @@
 #include <utility>
 
 #include "cm.cuh"
+#include "d3q19.cuh"
 #include "internal.h"
 
 namespace flbm {
@@ -36,16 +37,16 @@ namespace flbm {
 template <int D>
 struct StatsPlan {
   static constexpr int Q = Lat<D>::Q;
-  static constexpr int NC = D == 3 ? 32 : 16;  // columns, padded to whole MMA tiles
+  static constexpr int NC = D == 2 ? 16 : 32;  // columns, padded to whole MMA tiles
   static constexpr int LD = 32;                // shared-memory row: 32 words, swizzled (see swz)
   static constexpr int MT = NC / 16;           // 16-row tiles of G
   static constexpr int NT = NC / 8;            // 8-column tiles of G
   // Upper block-triangle: tiles (mt, nt) with nt >= 2 mt.
-  static constexpr int NTILE = D == 3 ? 6 : 2;
+  static constexpr int NTILE = D == 2 ? 2 : 6;
   static constexpr int NREC = NC * (NC + 1) / 2;
 };
 
-int stats_nacc(int Q) { return Q == 27 ? StatsPlan<3>::NREC : StatsPlan<2>::NREC; }
+int stats_nacc(int Q) { return Q == 9 ? StatsPlan<2>::NREC : StatsPlan<3>::NREC; }
 
 namespace {
 
@@ -54,11 +55,11 @@ constexpr int kFlushTiles = 8;
 
 template <int D>
 __host__ __device__ constexpr int tile_mt(int i) {
-  return D == 3 ? (i < 4 ? 0 : 1) : 0;
+  return D != 2 ? (i < 4 ? 0 : 1) : 0;
 }
 template <int D>
 __host__ __device__ constexpr int tile_nt(int i) {
-  return D == 3 ? (i < 4 ? i : i - 2) : i;
+  return D != 2 ? (i < 4 ? i : i - 2) : i;
 }
 
 // Shared-memory rows hold 32 words; column c of row r sits at word c ^ swz(r). With
@@ -66,6 +67,67 @@ __host__ __device__ constexpr int tile_nt(int i) {
 // and the fragment loads of an MMA step (rows s0 + t or s0 + t + 4, columns m0 + g) hit
 // 32 different banks.
 __device__ __forceinline__ int swz(int r) { return ((r & 3) << 3) | (((r >> 2) & 1) << 2); }
+
+// The D3Q19 columns of two sites s, s + 1 (lattice code 19): [1, rho - rho0, j, u,
+// k_4 .. k_18, 0 ...] from the generated transforms of d3q19_gen.cuh.
+template <typename S, int PARITY, bool PAIRROW>
+__device__ __forceinline__ void pair_columns19(const S *__restrict__ f, long long plane, int nx, int ny, int nz,
+                                               float rho0, long long s, long long N, float2 *col,
+                                               unsigned &nonfinite) {
+  float2 F[19];
+  const bool valid[2] = {s < N, s + 1 < N};
+  if (PAIRROW) {
+    if (valid[0]) {
+      const uint32_t r = (uint32_t)s / (uint32_t)nx, q = r / (uint32_t)ny;
+      const int x0 = (int)((uint32_t)s - r * (uint32_t)nx), y = (int)(r - q * (uint32_t)ny), z = (int)q;
+      load19_2<S, PARITY>(f, plane, addr2(x0, y, z, nx, ny, nz), F);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 19; ++a) F[a] = make_float2(0.0f, 0.0f);
+    }
+  } else {
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const long long sl = s + l;
+      float Fl[19];
+      if (valid[l]) {
+        const uint32_t r = (uint32_t)sl / (uint32_t)nx, q = r / (uint32_t)ny;
+        const int x = (int)((uint32_t)sl - r * (uint32_t)nx), y = (int)(r - q * (uint32_t)ny), z = (int)q;
+        load19<S, PARITY>(f, plane, neighbourhood(x, y, z, nx, ny, nz), Fl);
+      } else {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) Fl[a] = 0.0f;
+      }
+#pragma unroll
+      for (int a = 0; a < 19; ++a) set_lane(F[a], l, Fl[a]);
+    }
+  }
+  float2 r[19], rho, ux, uy, uz;
+  d3q19_macros(F, rho0, r, rho, ux, uy, uz);
+  const float2 drho = r[0];
+  d3q19_central(r, rho, ux, uy, uz);
+  col[0] = make_float2(valid[0] ? 1.0f : 0.0f, valid[1] ? 1.0f : 0.0f);
+  col[1] = drho;
+  col[2] = vmul(rho, ux);
+  col[3] = vmul(rho, uy);
+  col[4] = vmul(rho, uz);
+  col[5] = ux;
+  col[6] = uy;
+  col[7] = uz;
+#pragma unroll
+  for (int v = 4; v < 19; ++v) col[8 + v - 4] = r[v];
+  float2 sum = col[1];
+#pragma unroll
+  for (int c = 2; c < 8 + 15; ++c) sum = vadd(sum, col[c]);
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    if (valid[l] && !isfinite(lane(sum, l))) {
+      ++nonfinite;
+#pragma unroll
+      for (int c = 0; c < 8 + 15; ++c) set_lane(col[c], l, 0.0f);
+    }
+  }
+}
 
 // Round to TF32 (nearest, ties away): x_hi = tf32(x), x_lo = tf32(x - x_hi). Both are
 // rounded to nearest, so the split carries no bias (truncating x_lo would shrink every
@@ -208,7 +270,11 @@ __global__ void __launch_bounds__(kStatsBlock, 3) stats_kernel(const S *__restri
       float2 col[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) col[c] = make_float2(0.0f, 0.0f);
-      pair_columns<D, S, PARITY, PAIRROW, ISO>(f, plane, nx, ny, nz, rho0, base + 2 * threadIdx.x, N, col,
+      if constexpr (D == 19)
+        pair_columns19<S, PARITY, PAIRROW>(f, plane, nx, ny, nz, rho0, base + 2 * threadIdx.x, N, col,
+                                           nonfinite);
+      else
+        pair_columns<D, S, PARITY, PAIRROW, ISO>(f, plane, nx, ny, nz, rho0, base + 2 * threadIdx.x, N, col,
                                           nonfinite);
       // The two sites go to rows tid and tid + 128 (the sums do not depend on the order).
       const int r0 = threadIdx.x, r1 = threadIdx.x + kStatsBlock;
@@ -362,6 +428,12 @@ cudaError_t launch_typed(int parity, const void *f, long long plane, int nx, int
 
 cudaError_t launch_stats(int D, int storage, bool iso, int parity, const void *f, long long plane, int nx,
                          int ny, int nz, float rho0, double *acc, cudaStream_t s) {
+  if (D == 19) {  // D3Q19 (lattice code 19)
+    if (storage == 0) return launch_typed<19, float, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+    if (storage == 1)
+      return launch_typed<19, __nv_bfloat16, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+    return launch_typed<19, __half, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+  }
   if (D == 3 && iso) {
     if (storage == 0) return launch_typed<3, float, true>(parity, f, plane, nx, ny, nz, rho0, acc, s);
     if (storage == 1)

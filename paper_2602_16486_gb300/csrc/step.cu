@@ -30,9 +30,11 @@
 
 namespace flbm {
 
-cudaError_t launch_step(int D, int storage, int variant, int parity, bool noise, bool shear, bool iso,
+cudaError_t launch_step(int lattice, int storage, int variant, int parity, bool noise, bool shear,
                         const StepArgs &a, cudaStream_t s) {
-  if (iso) return launch_step_iso(storage, variant, parity, noise, shear, a, s);
+  if (lattice == 2) return launch_step_iso(storage, variant, parity, noise, shear, a, s);
+  if (lattice == 3) return launch_step_d3q19(storage, variant, parity, noise, shear, a, s);
+  const int D = lattice == 0 ? 2 : 3;
   if (storage != 0) return launch_step_16(D, storage, variant, parity, noise, shear, a, s);
   return D == 3 ? launch_typed<3, float, false>(variant, parity, noise, shear, a, s)
                 : launch_typed<2, float, false>(variant, parity, noise, shear, a, s);

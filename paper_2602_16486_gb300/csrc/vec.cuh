@@ -13,6 +13,12 @@ __device__ __forceinline__ float vsub(float a, float b) { return a - b; }
 __device__ __forceinline__ float vmul(float a, float b) { return a * b; }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 
+// FP64 forms, for set-up code that evaluates the same generated algebra in double.
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
+__device__ __forceinline__ double vmul(double a, double b) { return a * b; }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+
 __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -29,6 +35,26 @@ __device__ __forceinline__ float splat<float>(float x) {
 template <>
 __device__ __forceinline__ float2 splat<float2>(float x) {
   return make_float2(x, x);
+}
+template <>
+__device__ __forceinline__ double splat<double>(float x) {
+  return (double)x;
+}
+
+// A constant given in double, rounded once to the value type (generated code).
+template <typename T>
+__device__ __forceinline__ T rat(double x);
+template <>
+__device__ __forceinline__ float rat<float>(double x) {
+  return (float)x;
+}
+template <>
+__device__ __forceinline__ float2 rat<float2>(double x) {
+  return make_float2((float)x, (float)x);
+}
+template <>
+__device__ __forceinline__ double rat<double>(double x) {
+  return x;
 }
 
 // Number of sites a value of type T carries.

@@ -15,13 +15,13 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libflbm.so")
 
-FLBM_D2Q9, FLBM_D3Q27, FLBM_D3Q27_ISO = 0, 1, 2
+FLBM_D2Q9, FLBM_D3Q27, FLBM_D3Q27_ISO, FLBM_D3Q19 = 0, 1, 2, 3
 FLBM_FP32, FLBM_BF16, FLBM_FP16 = 0, 1, 2
 FLBM_OK, FLBM_EINVAL, FLBM_ENOMEM, FLBM_ECUDA, FLBM_ENUMERIC, FLBM_ETIMEOUT, FLBM_ESTATE = range(7)
 STATUS_NAMES = {0: "FLBM_OK", 1: "FLBM_EINVAL", 2: "FLBM_ENOMEM", 3: "FLBM_ECUDA",
                 4: "FLBM_ENUMERIC", 5: "FLBM_ETIMEOUT", 6: "FLBM_ESTATE"}
-Q_OF = {FLBM_D2Q9: 9, FLBM_D3Q27: 27, FLBM_D3Q27_ISO: 27}
-D_OF = {FLBM_D2Q9: 2, FLBM_D3Q27: 3, FLBM_D3Q27_ISO: 3}
+Q_OF = {FLBM_D2Q9: 9, FLBM_D3Q27: 27, FLBM_D3Q27_ISO: 27, FLBM_D3Q19: 19}
+D_OF = {FLBM_D2Q9: 2, FLBM_D3Q27: 3, FLBM_D3Q27_ISO: 3, FLBM_D3Q19: 3}
 
 
 class FlbmError(RuntimeError):
