@@ -145,7 +145,7 @@ __device__ __forceinline__ void collide19(T (&F)[19], float rho0, const float *o
     r[8] = vmul(splat<T>(om[8]), k8);
     r[9] = vmul(splat<T>(om[9]), k9);
   } else {
-    d3q19_central(r, rho, ux, uy, uz);
+    d3q19_central_lr(r, rho, ux, uy, uz);
 #pragma unroll
     for (int v = 4; v < 19; ++v) r[v] = vmul(splat<T>(om[v]), r[v]);
   }
@@ -164,7 +164,11 @@ __device__ __forceinline__ void collide19(T (&F)[19], float rho0, const float *o
       }
     }
   }
-  d3q19_raw_from_central(r, rho, ux, uy, uz);
+  // The general rates keep more values live; they use the register-lean inverse.
+  if (SHEAR)
+    d3q19_raw_from_central(r, rho, ux, uy, uz);
+  else
+    d3q19_raw_from_central_lr(r, rho, ux, uy, uz);
   r[0] = drho;  // populations as deviations from w rho0
   r[1] = jx;    // r*_a = j_a (momentum conserved)
   r[2] = jy;

@@ -329,6 +329,169 @@ __device__ __forceinline__ void d3q19_raw_from_central(T (&k)[19], T rho, T ux, 
   k[18] = x18;
 }
 
+// As d3q19_central, each row evaluating its own u-polynomials (fewer live registers).
+template <typename T>
+__device__ __forceinline__ void d3q19_central_lr(T (&r)[19], T rho, T ux, T uy, T uz) {
+  const T x4 = r[4]; const T x5 = r[5]; const T x6 = r[6]; const T x7 = r[7]; const T x8 = r[8]; const T x9 = r[9]; const T x10 = r[10]; const T x11 = r[11]; const T x12 = r[12]; const T x13 = r[13]; const T x14 = r[14]; const T x15 = r[15]; const T x16 = r[16]; const T x17 = r[17]; const T x18 = r[18];
+  {
+  r[4] = vfma(rho, vsub(vsub(vmul(rat<T>(-1.0), vmul(ux, ux)), vmul(uy, uy)), vmul(uz, uz)), x4);
+  }
+  {
+  r[5] = vfma(rho, vfma(rat<T>(-2.0), vmul(ux, ux), vadd(vmul(uy, uy), vmul(uz, uz))), x5);
+  }
+  {
+  r[6] = vfma(rho, vsub(vmul(uz, uz), vmul(uy, uy)), x6);
+  }
+  {
+  r[7] = vfma(rho, vmul(rat<T>(-1.0), vmul(ux, uy)), x7);
+  }
+  {
+  r[8] = vfma(rho, vmul(rat<T>(-1.0), vmul(uy, uz)), x8);
+  }
+  {
+  r[9] = vfma(rho, vmul(rat<T>(-1.0), vmul(ux, uz)), x9);
+  }
+  {
+    const T g10_0 = vmul(rat<T>(6.0), ux);
+  r[10] = vfma(vmul(rat<T>(-6.0), uz), x9, vfma(vmul(rat<T>(-6.0), uy), x7, vfma(vmul(rat<T>(-2.0), ux), x5, vfma(vmul(rat<T>(-5.0), ux), x4, vfma(rho, vadd(vadd(vmul(rat<T>(6.0), vmul(vmul(ux, ux), ux)), vmul(vmul(g10_0, uy), uy)), vmul(vmul(g10_0, uz), uz)), x10)))));
+  }
+  {
+    const T g11_0 = vmul(rat<T>(6.0), uy);
+  r[11] = vfma(vmul(rat<T>(-6.0), uz), x8, vfma(vmul(rat<T>(-6.0), ux), x7, vfma(vmul(rat<T>(-3.0), uy), x6, vfma(uy, x5, vfma(vmul(rat<T>(-5.0), uy), x4, vfma(rho, vadd(vadd(vmul(rat<T>(6.0), vmul(vmul(uy, uy), uy)), vmul(vmul(g11_0, ux), ux)), vmul(vmul(g11_0, uz), uz)), x11))))));
+  }
+  {
+    const T g12_0 = vmul(rat<T>(6.0), uz);
+  r[12] = vfma(vmul(rat<T>(-6.0), ux), x9, vfma(vmul(rat<T>(-6.0), uy), x8, vfma(vmul(rat<T>(3.0), uz), x6, vfma(uz, x5, vfma(vmul(rat<T>(-5.0), uz), x4, vfma(rho, vadd(vadd(vmul(rat<T>(6.0), vmul(vmul(uz, uz), uz)), vmul(vmul(g12_0, ux), ux)), vmul(vmul(g12_0, uy), uy)), x12))))));
+  }
+  {
+    const T g13_0 = vmul(rat<T>(2.0), ux);
+  r[13] = vfma(vmul(rat<T>(2.0), uz), x9, vfma(vmul(rat<T>(-2.0), uy), x7, vfma(vmul(rat<T>(-1.0), ux), x6, vfma(rho, vsub(vmul(vmul(g13_0, uy), uy), vmul(vmul(g13_0, uz), uz)), x13))));
+  }
+  {
+    const T g14_0 = vmul(rat<T>(0.5), uy);
+  r[14] = vfma(vmul(rat<T>(-2.0), uz), x8, vfma(vmul(rat<T>(2.0), ux), x7, vfma(g14_0, x6, vfma(g14_0, x5, vfma(rho, vfma(rat<T>(-2.0), vmul(vmul(uy, ux), ux), vmul(rat<T>(2.0), vmul(vmul(uy, uz), uz))), x14)))));
+  }
+  {
+    const T g15_0 = vmul(rat<T>(2.0), uz);
+    const T g15_1 = vmul(rat<T>(0.5), uz);
+  r[15] = vfma(vmul(rat<T>(-2.0), ux), x9, vfma(vmul(rat<T>(2.0), uy), x8, vfma(g15_1, x6, vfma(vmul(rat<T>(-1.0), g15_1), x5, vfma(rho, vsub(vmul(vmul(g15_0, ux), ux), vmul(vmul(g15_0, uy), uy)), x15)))));
+  }
+  {
+    const T g16_0 = vmul(ux, ux);
+    const T g16_1 = vmul(rat<T>(4.0), g16_0);
+    const T g16_2 = vmul(uy, uy);
+    const T g16_3 = vmul(uz, uz);
+    const T g16_4 = vmul(rat<T>(18.0), g16_0);
+    const T g16_5 = vmul(rat<T>(24.0), uy);
+  r[16] = vfma(vmul(rat<T>(-4.0), uz), x12, vfma(vmul(rat<T>(-4.0), uy), x11, vfma(vmul(rat<T>(-4.0), ux), x10, vfma(vmul(rat<T>(24.0), vmul(ux, uz)), x9, vfma(vmul(g16_5, uz), x8, vfma(vmul(g16_5, ux), x7, vfma(vfma(rat<T>(-6.0), g16_3, vmul(rat<T>(6.0), g16_2)), x6, vfma(vfma(rat<T>(-2.0), g16_3, vfma(rat<T>(-2.0), g16_2, g16_1)), x5, vfma(vfma(rat<T>(10.0), g16_3, vfma(rat<T>(10.0), g16_2, vmul(rat<T>(10.0), g16_0))), x4, vfma(rho, vsub(vsub(vsub(vfma(rat<T>(-9.0), vmul(vmul(vmul(uz, uz), uz), uz), vfma(rat<T>(-9.0), vmul(vmul(vmul(uy, uy), uy), uy), vfma(rat<T>(-9.0), vmul(vmul(vmul(ux, ux), ux), ux), vfma(rat<T>(-4.0), g16_3, vfma(rat<T>(-4.0), g16_2, vmul(rat<T>(-18.0), vmul(g16_2, g16_3))))))), g16_1), vmul(g16_2, g16_4)), vmul(g16_3, g16_4)), x16))))))))));
+  }
+  {
+    const T g17_0 = vmul(ux, ux);
+    const T g17_1 = vmul(uy, uy);
+    const T g17_2 = vmul(uz, uz);
+    const T g17_3 = vmul(rat<T>(6.0), g17_0);
+    const T g17_4 = vmul(rat<T>(8.0), ux);
+  r[17] = vfma(vmul(rat<T>(-6.0), uz), x15, vfma(vmul(rat<T>(6.0), uy), x14, vfma(vmul(rat<T>(0.6666666666666666), uz), x12, vfma(vmul(rat<T>(0.6666666666666666), uy), x11, vfma(vmul(rat<T>(-1.3333333333333333), ux), x10, vfma(vmul(g17_4, uz), x9, vfma(vmul(rat<T>(-16.0), vmul(uy, uz)), x8, vfma(vmul(g17_4, uy), x7, vfma(vfma(rat<T>(-4.0), g17_1, vmul(rat<T>(4.0), g17_2)), x6, vfma(vfma(rat<T>(7.333333333333333), g17_0, vfma(rat<T>(3.3333333333333335), g17_2, vmul(rat<T>(3.3333333333333335), g17_1))), x5, vfma(vfma(rat<T>(-4.666666666666667), g17_2, vfma(rat<T>(-4.666666666666667), g17_1, vmul(rat<T>(9.333333333333334), g17_0))), x4, vfma(rho, vsub(vsub(vfma(rat<T>(-12.0), vmul(vmul(vmul(ux, ux), ux), ux), vfma(rat<T>(-3.3333333333333335), g17_0, vfma(rat<T>(6.0), vmul(vmul(vmul(uz, uz), uz), uz), vfma(rat<T>(6.0), vmul(vmul(vmul(uy, uy), uy), uy), vfma(rat<T>(1.6666666666666667), g17_2, vfma(rat<T>(1.6666666666666667), g17_1, vmul(rat<T>(12.0), vmul(g17_1, g17_2)))))))), vmul(g17_1, g17_3)), vmul(g17_2, g17_3)), x17))))))))))));
+  }
+  {
+    const T g18_0 = vmul(uy, uy);
+    const T g18_1 = vmul(uz, uz);
+    const T g18_2 = vmul(ux, ux);
+    const T g18_3 = vmul(rat<T>(6.0), g18_0);
+    const T g18_4 = vmul(rat<T>(8.0), ux);
+  r[18] = vfma(vmul(rat<T>(2.0), uz), x15, vfma(vmul(rat<T>(2.0), uy), x14, vfma(vmul(rat<T>(-4.0), ux), x13, vfma(vmul(rat<T>(0.6666666666666666), uz), x12, vfma(vmul(rat<T>(-0.6666666666666666), uy), x11, vfma(vmul(rat<T>(-1.0), vmul(g18_4, uz)), x9, vfma(vmul(g18_4, uy), x7, vfma(vadd(vfma(rat<T>(6.0), g18_1, vmul(rat<T>(2.0), g18_2)), g18_3), x6, vfma(vfma(rat<T>(-1.3333333333333333), g18_0, vmul(rat<T>(1.3333333333333333), g18_1)), x5, vfma(vfma(rat<T>(-4.666666666666667), g18_1, vmul(rat<T>(4.666666666666667), g18_0)), x4, vfma(rho, vsub(vfma(rat<T>(-6.0), vmul(vmul(vmul(uy, uy), uy), uy), vfma(rat<T>(-1.6666666666666667), g18_0, vfma(rat<T>(6.0), vmul(vmul(vmul(uz, uz), uz), uz), vfma(rat<T>(6.0), vmul(g18_1, g18_2), vmul(rat<T>(1.6666666666666667), g18_1))))), vmul(g18_2, g18_3)), x18)))))))))));
+  }
+}
+
+// As d3q19_raw_from_central, each row evaluating its own u-polynomials.
+template <typename T>
+__device__ __forceinline__ void d3q19_raw_from_central_lr(T (&k)[19], T rho, T ux, T uy, T uz) {
+  T x4; T x5; T x6; T x7; T x8; T x9; T x10; T x11; T x12; T x13; T x14; T x15; T x16; T x17; T x18;
+  const T k4 = k[4]; const T k5 = k[5]; const T k6 = k[6]; const T k7 = k[7]; const T k8 = k[8]; const T k9 = k[9]; const T k10 = k[10]; const T k11 = k[11]; const T k12 = k[12]; const T k13 = k[13]; const T k14 = k[14]; const T k15 = k[15]; const T k16 = k[16]; const T k17 = k[17]; const T k18 = k[18];
+  {
+  x4 = vfma(rho, vadd(vadd(vmul(ux, ux), vmul(uy, uy)), vmul(uz, uz)), k4);
+    k[4] = x4;
+  }
+  {
+  x5 = vfma(rho, vsub(vsub(vmul(rat<T>(2.0), vmul(ux, ux)), vmul(uy, uy)), vmul(uz, uz)), k5);
+    k[5] = x5;
+  }
+  {
+  x6 = vfma(rho, vsub(vmul(uy, uy), vmul(uz, uz)), k6);
+    k[6] = x6;
+  }
+  {
+  x7 = vfma(rho, vmul(ux, uy), k7);
+    k[7] = x7;
+  }
+  {
+  x8 = vfma(rho, vmul(uy, uz), k8);
+    k[8] = x8;
+  }
+  {
+  x9 = vfma(rho, vmul(ux, uz), k9);
+    k[9] = x9;
+  }
+  {
+    const T h10_0 = vmul(rat<T>(6.0), ux);
+  x10 = vfma(vmul(rat<T>(6.0), uz), x9, vfma(vmul(rat<T>(6.0), uy), x7, vfma(vmul(rat<T>(2.0), ux), x5, vfma(vmul(rat<T>(5.0), ux), x4, vfma(rho, vsub(vsub(vmul(rat<T>(-6.0), vmul(vmul(ux, ux), ux)), vmul(vmul(h10_0, uy), uy)), vmul(vmul(h10_0, uz), uz)), k10)))));
+    k[10] = x10;
+  }
+  {
+    const T h11_0 = vmul(rat<T>(6.0), uy);
+  x11 = vfma(vmul(rat<T>(6.0), uz), x8, vfma(vmul(rat<T>(6.0), ux), x7, vfma(vmul(rat<T>(3.0), uy), x6, vfma(vmul(rat<T>(-1.0), uy), x5, vfma(vmul(rat<T>(5.0), uy), x4, vfma(rho, vsub(vsub(vmul(rat<T>(-6.0), vmul(vmul(uy, uy), uy)), vmul(vmul(h11_0, ux), ux)), vmul(vmul(h11_0, uz), uz)), k11))))));
+    k[11] = x11;
+  }
+  {
+    const T h12_0 = vmul(rat<T>(6.0), uz);
+  x12 = vfma(vmul(rat<T>(6.0), ux), x9, vfma(vmul(rat<T>(6.0), uy), x8, vfma(vmul(rat<T>(-3.0), uz), x6, vfma(vmul(rat<T>(-1.0), uz), x5, vfma(vmul(rat<T>(5.0), uz), x4, vfma(rho, vsub(vsub(vmul(rat<T>(-6.0), vmul(vmul(uz, uz), uz)), vmul(vmul(h12_0, ux), ux)), vmul(vmul(h12_0, uy), uy)), k12))))));
+    k[12] = x12;
+  }
+  {
+  x13 = vfma(vmul(rat<T>(-2.0), uz), x9, vfma(vmul(rat<T>(2.0), uy), x7, vfma(ux, x6, vfma(rho, vfma(rat<T>(-2.0), vmul(vmul(ux, uy), uy), vmul(rat<T>(2.0), vmul(vmul(ux, uz), uz))), k13))));
+    k[13] = x13;
+  }
+  {
+    const T h14_0 = vmul(rat<T>(2.0), uy);
+    const T h14_1 = vmul(rat<T>(-0.5), uy);
+  x14 = vfma(vmul(rat<T>(2.0), uz), x8, vfma(vmul(rat<T>(-2.0), ux), x7, vfma(h14_1, x6, vfma(h14_1, x5, vfma(rho, vsub(vmul(vmul(h14_0, ux), ux), vmul(vmul(h14_0, uz), uz)), k14)))));
+    k[14] = x14;
+  }
+  {
+    const T h15_0 = vmul(rat<T>(0.5), uz);
+  x15 = vfma(vmul(rat<T>(2.0), ux), x9, vfma(vmul(rat<T>(-2.0), uy), x8, vfma(vmul(rat<T>(-1.0), h15_0), x6, vfma(h15_0, x5, vfma(rho, vfma(rat<T>(-2.0), vmul(vmul(uz, ux), ux), vmul(rat<T>(2.0), vmul(vmul(uz, uy), uy))), k15)))));
+    k[15] = x15;
+  }
+  {
+    const T h16_0 = vmul(ux, ux);
+    const T h16_1 = vmul(rat<T>(4.0), h16_0);
+    const T h16_2 = vmul(uy, uy);
+    const T h16_3 = vmul(uz, uz);
+    const T h16_4 = vmul(rat<T>(18.0), h16_0);
+    const T h16_5 = vmul(rat<T>(24.0), uy);
+  x16 = vfma(vmul(rat<T>(4.0), uz), x12, vfma(vmul(rat<T>(4.0), uy), x11, vfma(vmul(rat<T>(4.0), ux), x10, vfma(vmul(rat<T>(-24.0), vmul(ux, uz)), x9, vfma(vmul(rat<T>(-1.0), vmul(h16_5, uz)), x8, vfma(vmul(rat<T>(-1.0), vmul(h16_5, ux)), x7, vfma(vfma(rat<T>(-6.0), h16_2, vmul(rat<T>(6.0), h16_3)), x6, vfma(vsub(vfma(rat<T>(2.0), h16_3, vmul(rat<T>(2.0), h16_2)), h16_1), x5, vfma(vfma(rat<T>(-10.0), h16_3, vfma(rat<T>(-10.0), h16_2, vmul(rat<T>(-10.0), h16_0))), x4, vfma(rho, vadd(vadd(vadd(vfma(rat<T>(9.0), vmul(vmul(vmul(uz, uz), uz), uz), vfma(rat<T>(9.0), vmul(vmul(vmul(uy, uy), uy), uy), vfma(rat<T>(9.0), vmul(vmul(vmul(ux, ux), ux), ux), vfma(rat<T>(4.0), h16_3, vfma(rat<T>(4.0), h16_2, vmul(rat<T>(18.0), vmul(h16_2, h16_3))))))), h16_1), vmul(h16_2, h16_4)), vmul(h16_3, h16_4)), k16))))))))));
+    k[16] = x16;
+  }
+  {
+    const T h17_0 = vmul(ux, ux);
+    const T h17_1 = vmul(uy, uy);
+    const T h17_2 = vmul(uz, uz);
+    const T h17_3 = vmul(rat<T>(8.0), ux);
+  x17 = vfma(vmul(rat<T>(6.0), uz), x15, vfma(vmul(rat<T>(-6.0), uy), x14, vfma(vmul(rat<T>(-0.6666666666666666), uz), x12, vfma(vmul(rat<T>(-0.6666666666666666), uy), x11, vfma(vmul(rat<T>(1.3333333333333333), ux), x10, vfma(vmul(rat<T>(-1.0), vmul(h17_3, uz)), x9, vfma(vmul(rat<T>(16.0), vmul(uy, uz)), x8, vfma(vmul(rat<T>(-1.0), vmul(h17_3, uy)), x7, vfma(vfma(rat<T>(-4.0), h17_2, vmul(rat<T>(4.0), h17_1)), x6, vfma(vfma(rat<T>(-7.333333333333333), h17_0, vfma(rat<T>(-3.3333333333333335), h17_2, vmul(rat<T>(-3.3333333333333335), h17_1))), x5, vfma(vfma(rat<T>(-9.333333333333334), h17_0, vfma(rat<T>(4.666666666666667), h17_2, vmul(rat<T>(4.666666666666667), h17_1))), x4, vfma(rho, vfma(rat<T>(-6.0), vmul(vmul(vmul(uz, uz), uz), uz), vfma(rat<T>(-6.0), vmul(vmul(vmul(uy, uy), uy), uy), vfma(rat<T>(-1.6666666666666667), h17_2, vfma(rat<T>(-1.6666666666666667), h17_1, vfma(rat<T>(-12.0), vmul(h17_1, h17_2), vfma(rat<T>(6.0), vmul(h17_0, h17_2), vfma(rat<T>(6.0), vmul(h17_0, h17_1), vfma(rat<T>(12.0), vmul(vmul(vmul(ux, ux), ux), ux), vmul(rat<T>(3.3333333333333335), h17_0))))))))), k17))))))))))));
+    k[17] = x17;
+  }
+  {
+    const T h18_0 = vmul(uy, uy);
+    const T h18_1 = vmul(uz, uz);
+    const T h18_2 = vmul(ux, ux);
+    const T h18_3 = vmul(rat<T>(6.0), h18_0);
+    const T h18_4 = vmul(rat<T>(6.0), h18_1);
+    const T h18_5 = vmul(rat<T>(8.0), ux);
+  x18 = vfma(vmul(rat<T>(-2.0), uz), x15, vfma(vmul(rat<T>(-2.0), uy), x14, vfma(vmul(rat<T>(4.0), ux), x13, vfma(vmul(rat<T>(-0.6666666666666666), uz), x12, vfma(vmul(rat<T>(0.6666666666666666), uy), x11, vfma(vmul(h18_5, uz), x9, vfma(vmul(rat<T>(-1.0), vmul(h18_5, uy)), x7, vfma(vsub(vsub(vmul(rat<T>(-2.0), h18_2), h18_3), h18_4), x6, vfma(vfma(rat<T>(-1.3333333333333333), h18_1, vmul(rat<T>(1.3333333333333333), h18_0)), x5, vfma(vfma(rat<T>(-4.666666666666667), h18_0, vmul(rat<T>(4.666666666666667), h18_1)), x4, vfma(rho, vsub(vfma(rat<T>(-6.0), vmul(vmul(vmul(uz, uz), uz), uz), vfma(rat<T>(-1.6666666666666667), h18_1, vadd(vfma(rat<T>(6.0), vmul(vmul(vmul(uy, uy), uy), uy), vmul(rat<T>(1.6666666666666667), h18_0)), vmul(h18_2, h18_3)))), vmul(h18_2, h18_4)), k18)))))))))));
+    k[18] = x18;
+  }
+}
+
 // Deviations d*_i = sum_v w_i M_vi r*_v / b_v (M^{-1} = W M^T B^{-1}); r*_0 = rho - rho0.
 template <typename T>
 __device__ __forceinline__ void d3q19_pop(const T (&r)[19], T (&f)[19]) {

@@ -176,6 +176,34 @@ def shift_rows(sign, prefix, src, dst_fmt):
     return "\n".join(lines)
 
 
+def shift_rows_local(sign, prefix, src, dst_fmt):
+    """As shift_rows, but each row evaluates its own u-polynomials inside a block, so that
+    no polynomial stays live across rows (fewer registers, some repeated products)."""
+    lines = []
+    for v in range(4, 19):
+        keys, polys = [], []
+        if P[v] != 0:
+            keys.append(("P", v, None))
+            polys.append(sign * P[v])
+        for w in range(4, v):
+            if N[v, w] != 0:
+                keys.append(("N", v, w))
+                polys.append(sign * N[v, w])
+        reps, red = sp.cse(polys, symbols=sp.numbered_symbols(f"{prefix}{v}_"), optimizations=None)
+        lines.append("  {")
+        lines += [f"    const T {t} = {emit(e)};" for t, e in reps]
+        acc = f"{src}{v}"
+        for key, e in zip(keys, red):
+            term = emit(e)
+            if key[0] == "P":
+                acc = f"vfma(rho, {term}, {acc})"
+            else:
+                acc = f"vfma({term}, x{key[2]}, {acc})"
+        lines.append("  " + dst_fmt.format(v=v, code=acc).replace("\n", "\n  "))
+        lines.append("  }")
+    return "\n".join(lines)
+
+
 # forward central transform, in place, rows 4..18 (every row reads raw values)
 out.append("// Central moments k_v, v = 4..18, in place over the raw moments r (r_0..3 are not read:\n"
            "// the shift uses r_0 = rho and r_a = rho u_a).")
@@ -199,6 +227,20 @@ out.append("template <typename T>\n__device__ __forceinline__ void d3q19_raw_fro
            "T uy, T uz) {")
 out.append("  " + " ".join(f"const T k{v} = k[{v}];" for v in range(4, 19)))
 out.append(shift_rows(-1, "d", "k", "  const T x{v} = {code};\n  k[{v}] = x{v};"))
+out.append("}\n")
+# the same two shifts with per-row polynomials (register-lean forms)
+out.append("// As d3q19_central, each row evaluating its own u-polynomials (fewer live registers).")
+out.append("template <typename T>\n__device__ __forceinline__ void d3q19_central_lr(T (&r)[19], T rho, T ux, T uy, "
+           "T uz) {")
+out.append("  " + " ".join(f"const T x{w} = r[{w}];" for w in range(4, 19)))
+out.append(shift_rows_local(1, "g", "x", "r[{v}] = {code};"))
+out.append("}\n")
+out.append("// As d3q19_raw_from_central, each row evaluating its own u-polynomials.")
+out.append("template <typename T>\n__device__ __forceinline__ void d3q19_raw_from_central_lr(T (&k)[19], T rho, T ux, "
+           "T uy, T uz) {")
+out.append("  " + " ".join(f"T x{v};" for v in range(4, 19)))
+out.append("  " + " ".join(f"const T k{v} = k[{v}];" for v in range(4, 19)))
+out.append(shift_rows_local(-1, "h", "k", "x{v} = {code};\n  k[{v}] = x{v};"))
 out.append("}\n")
 # populations from raw moments: f = W M^T B^{-1} r
 out.append("// Deviations d*_i = sum_v w_i M_vi r*_v / b_v (M^{-1} = W M^T B^{-1}); r*_0 = rho - rho0.")
