@@ -76,8 +76,8 @@ def measured_peaks():
 
 # Sources the single-lattice step kernels are compiled from (a change to any of them
 # invalidates recorded DRAM counters).
-STEP_SOURCES = ("step.cu", "step_pipe.cu", "async.cuh", "cm.cuh", "collide.cuh", "philox.cuh", "lattice.cuh",
-                "vec.cuh", "internal.h")
+STEP_SOURCES = ("step.cu", "step_kernels.cuh", "step_pipe.cu", "async.cuh", "cm.cuh", "collide.cuh", "philox.cuh",
+                "lattice.cuh", "vec.cuh", "internal.h")
 
 
 def kernel_source_hash():
