@@ -841,12 +841,12 @@ int batch_params(flbm_batch *b) {
   return FLBM_OK;
 }
 
-// Tiling for the block size b->threads (tiles of 2 * threads sites, never spanning
-// lattices; lattice i owns tiles [tile0_i, tile0_{i+1})) and the grid of co-resident
-// blocks.
+// Tiling for the block size b->threads (tiles of `threads` pair slots, never spanning
+// lattices; a row of nx sites holds ceil(nx / 2) slots; lattice i owns tiles
+// [tile0_i, tile0_{i+1})) and the grid of co-resident blocks.
 int batch_shape(flbm_batch *b) {
   if (b->tiles_for == b->threads) return FLBM_OK;
-  const long long span = 2LL * b->threads;
+  const long long per_tile = b->threads;
   long long total = 0;
   const int nl = int(b->members.size());
   int n3 = 0;  // table entries 0 .. n3-1 are the D3Q27 lattices
@@ -855,7 +855,9 @@ int batch_shape(flbm_batch *b) {
   for (int i = 0; i < nl; ++i) {
     if (i == n3) tiles3 = total;
     b->args->lats[i].tile0 = int(total);
-    total += (b->members[size_t(b->order[size_t(i)])]->N + span - 1) / span;
+    const flbm_ctx *m = b->members[size_t(b->order[size_t(i)])];
+    const long long slots = (m->dims[0] + 1) / 2 * m->dims[1] * m->dims[2];
+    total += (slots + per_tile - 1) / per_tile;
     if (total > 0x3fffffffLL) return fail(FLBM_EINVAL, "too many tiles");
   }
   if (n3 == nl) tiles3 = total;
@@ -881,7 +883,7 @@ int batch_enqueue(flbm_batch *b, int64_t n) {
   b->args->rates = b->d_rates;
   b->args->nlat = int(b->members.size());
   b->args->ntiles = b->ntiles;
-  b->args->span = 2 * b->threads;
+  b->args->tile_slots = b->threads;
   b->args->nsteps = int(n);
   b->args->step_counter = b->d_step;
   b->args->done = b->d_done;

@@ -2,8 +2,8 @@
 // rates, kBT and noise seed) advanced by one persistent kernel.
 //
 // The host lays every lattice's populations out in one allocation and cuts all lattices
-// into tiles of equal site count (two sites per thread; a tile may span rows, never
-// lattices). One cooperative launch runs n steps: block b takes the work items
+// into tiles of equal pair-slot count (one slot of two x-adjacent sites per thread; a
+// tile may span rows, never lattices). One cooperative launch runs n steps: block b takes the work items
 // (step s, tile b + j G) in step-major order, and applies to each the same fused update
 // as the single-lattice kernels (collide.cuh: rolled noise loop, packed FP32x2, the AA
 // pattern of step.cu) with that lattice's parameters.
@@ -53,85 +53,162 @@ __device__ __forceinline__ void collide_lattice(float2 (&F)[3][3][3], const Batc
                                                   keys, dsite);
 }
 
-// Coordinates of site s of lattice L (32-bit arithmetic: every site index is < 2^32).
-__device__ __forceinline__ void site_xyz(const BatchLattice &L, uint32_t s, int &x, int &y, int &z) {
-  const uint32_t r = s / (uint32_t)L.nx;
-  x = (int)(s - r * (uint32_t)L.nx);
+// Pair slots of lattice L: row r = y + ny z holds ceil(nx / 2) slots, and slot j of it
+// is the sites x0 = 2 j and x0 + 1 (only x0 in the last slot of a row when nx is odd).
+// Slots are numbered row-major, so consecutive slots are consecutive sites and a warp's
+// accesses stay contiguous for every nx.
+__device__ __forceinline__ uint32_t pair_slots(const BatchLattice &L) {
+  return (uint32_t)((L.nx + 1) >> 1) * (uint32_t)L.ny * (uint32_t)L.nz;
+}
+
+// Row coordinates of pair slot `slot` (32-bit arithmetic: every site index is < 2^32)
+// and the site index of its first site: 2 slot when nx is even, 2 slot - r otherwise.
+__device__ __forceinline__ uint32_t slot_xyz(const BatchLattice &L, uint32_t slot, int &x0, int &y, int &z) {
+  const uint32_t hp = (uint32_t)((L.nx + 1) >> 1);
+  const uint32_t r = slot / hp;
+  x0 = 2 * (int)(slot - r * hp);
   const uint32_t q = r / (uint32_t)L.ny;
   y = (int)(r - q * (uint32_t)L.ny);
   z = (int)q;
+  return 2u * slot - ((L.nx & 1) ? r : 0u);
 }
 
-// Two sites of lattice L per thread, in tile [first, end). PAIR (nx even): sites
-// first + 2 t and first + 2 t + 1 share a row and move as pairs (8-byte accesses).
-// Otherwise (nx odd) lane l takes site first + t + l * blockDim.x, so that every access
-// of a warp is a contiguous run. Either way the neighbour addresses are recomputed at
-// the store rather than kept live across the collision (register pressure).
-template <int D, int PARITY, bool SHEAR, bool PAIR, bool ROLLED = true>
-__device__ __forceinline__ void batch_sites(const BatchLattice &L, const float *rates, uint32_t first, uint32_t end,
+// Sites of a pair slot of an odd-nx row: x0 - 1, x0, x0 + 1 and x0 + 2 (periodic), and
+// the periodic row / plane offsets as in Addr2. Lane 0 is site x0 and uses s[0..2]; lane
+// 1 is x0 + 1 and uses s[1..3]. In the last slot of a row (x0 = nx - 1) lane 1 wraps to
+// a real site of the same row: it is loaded and collided (every access stays inside the
+// lattice) but never stored.
+struct OddPair {
+  long long s[4];
+  long long dy[3], dz[3];
+};
+
+__device__ __forceinline__ OddPair odd_pair(int x0, int y, int z, int nx, int ny, int nz) {
+  OddPair a;
+  const long long row = ((long long)z * ny + y) * nx;
+  int x1 = x0 + 1;
+  if (x1 >= nx) x1 -= nx;
+  int x2 = x1 + 1;
+  if (x2 >= nx) x2 -= nx;
+  a.s[0] = row + (x0 == 0 ? nx - 1 : x0 - 1);
+  a.s[1] = row + x0;
+  a.s[2] = row + x1;
+  a.s[3] = row + x2;
+  const long long rl = nx, pl = (long long)nx * ny;
+  a.dy[0] = (y == 0) ? (long long)(ny - 1) * rl : -rl;
+  a.dy[1] = 0;
+  a.dy[2] = (y == ny - 1) ? -(long long)(ny - 1) * rl : rl;
+  a.dz[0] = (z == 0) ? (long long)(nz - 1) * pl : -pl;
+  a.dz[1] = 0;
+  a.dz[2] = (z == nz - 1) ? -(long long)(nz - 1) * pl : pl;
+  return a;
+}
+
+// As load_logical2 for an odd-nx pair: scalar accesses (the pair is not 8-byte aligned).
+template <int D, int PARITY>
+__device__ __forceinline__ void load_odd_pair(const float *__restrict__ f, long long plane, const OddPair &ad,
+                                              float2 (&F)[3][3][3]) {
+  constexpr int z0 = (D == 3) ? -1 : 0, z1 = (D == 3) ? 1 : 0;
+#pragma unroll
+  for (int dz = z0; dz <= z1; ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = Lat<D>::index(dx, dy, dz);
+        float2 v;
+        if (PARITY == 0) {
+          const float *b = f + i * plane;
+          v.x = b[ad.s[1]];
+          v.y = b[ad.s[2]];
+        } else {
+          // f_i(x) = A[opposite(i)][x - c_i]
+          const float *b = f + opposite<D>(i) * plane + ad.dy[1 - dy] + ad.dz[1 - dz];
+          v.x = b[ad.s[1 - dx]];
+          v.y = b[ad.s[2 - dx]];
+        }
+        F[dz + 1][dy + 1][dx + 1] = v;
+      }
+}
+
+// As store_streamed2 for an odd-nx pair; lane 1 only when `two`.
+template <int D, int PARITY>
+__device__ __forceinline__ void store_odd_pair(float *__restrict__ f, long long plane, const OddPair &ad, bool two,
+                                               const float2 (&F)[3][3][3]) {
+  constexpr int z0 = (D == 3) ? -1 : 0, z1 = (D == 3) ? 1 : 0;
+#pragma unroll
+  for (int dz = z0; dz <= z1; ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = Lat<D>::index(dx, dy, dz);
+        const float2 v = F[dz + 1][dy + 1][dx + 1];
+        float *b;
+        int k0, k1;
+        if (PARITY == 0) {
+          b = f + opposite<D>(i) * plane;
+          k0 = 1;
+          k1 = 2;
+        } else {
+          // f*_i(x) goes to A[i][x + c_i]
+          b = f + i * plane + ad.dy[1 + dy] + ad.dz[1 + dz];
+          k0 = 1 + dx;
+          k1 = 2 + dx;
+        }
+        b[ad.s[k0]] = v.x;
+        if (two) b[ad.s[k1]] = v.y;
+      }
+}
+
+// The two sites of pair slot `slot` of lattice L. EVEN (nx even): the sites share a row
+// and move as 8-byte pairs (Addr2, as the single-lattice kernels). Otherwise scalar
+// accesses through OddPair. Either way the neighbour addresses are recomputed at the
+// store rather than kept live across the collision (register pressure).
+template <int D, int PARITY, bool SHEAR, bool EVEN, bool ROLLED = true>
+__device__ __forceinline__ void batch_sites(const BatchLattice &L, const float *rates, uint32_t slot,
                                             uint32_t step_lo, uint32_t step_hi) {
   float *__restrict__ f = static_cast<float *>(L.f);
   const long long plane = L.plane;
   float2 F[3][3][3];
-  if (PAIR) {
-    const uint32_t s0 = first + 2u * threadIdx.x;
-    if (s0 >= end) return;
-    {
-      int x0, y, z;
-      site_xyz(L, s0, x0, y, z);
-      load_logical2<D, float, PARITY>(f, plane, addr2(x0, y, z, L.nx, L.ny, L.nz), F);
-    }
-    collide_lattice<D, SHEAR, ROLLED>(F, L, rates, s0, 1u, step_lo, step_hi);
-    // The neighbour addresses (18 registers) are rebuilt from the site index for the
-    // store instead of being kept across the collision; the empty asm hides s0's
-    // provenance so that the compiler cannot merge the two computations.
-    uint32_t s1 = s0;
-    asm volatile("" : "+r"(s1));
+  uint32_t s0;
+  {
     int x0, y, z;
-    site_xyz(L, s1, x0, y, z);
-    store_streamed2<D, float, PARITY>(f, plane, addr2(x0, y, z, L.nx, L.ny, L.nz), F);
-  } else {
-    const uint32_t T = blockDim.x;
-    const uint32_t s0 = first + threadIdx.x;
-    if (s0 >= end) return;
-    const bool second = s0 + T < end;
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      const uint32_t s = (l == 1 && second) ? s0 + T : s0;  // an absent second lane repeats the first
-      int x, y, z;
-      site_xyz(L, s, x, y, z);
-      float Fl[3][3][3];
-      load_logical<D, float, PARITY>(f, plane, neighbourhood(x, y, z, L.nx, L.ny, L.nz), Fl);
-#pragma unroll
-      for (int a = 0; a < 27; ++a) set_lane((&F[0][0][0])[a], l, (&Fl[0][0][0])[a]);
-    }
-    collide_lattice<D, SHEAR, ROLLED>(F, L, rates, s0, T, step_lo, step_hi);
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      if (l == 1 && !second) break;
-      int x, y, z;
-      site_xyz(L, s0 + (uint32_t)l * T, x, y, z);
-      float Fl[3][3][3];
-#pragma unroll
-      for (int a = 0; a < 27; ++a) (&Fl[0][0][0])[a] = lane((&F[0][0][0])[a], l);
-      store_streamed<D, float, PARITY>(f, plane, neighbourhood(x, y, z, L.nx, L.ny, L.nz), Fl);
-    }
+    s0 = slot_xyz(L, slot, x0, y, z);
+    if (EVEN)
+      load_logical2<D, float, PARITY>(f, plane, addr2(x0, y, z, L.nx, L.ny, L.nz), F);
+    else
+      load_odd_pair<D, PARITY>(f, plane, odd_pair(x0, y, z, L.nx, L.ny, L.nz), F);
   }
+  collide_lattice<D, SHEAR, ROLLED>(F, L, rates, s0, 1u, step_lo, step_hi);
+  // The empty asm hides the slot's provenance so that the compiler cannot merge the
+  // store's address computation with the load's (and keep 18 registers live).
+  uint32_t sl = slot;
+  asm volatile("" : "+r"(sl));
+  int x0, y, z;
+  slot_xyz(L, sl, x0, y, z);
+  if (EVEN)
+    store_streamed2<D, float, PARITY>(f, plane, addr2(x0, y, z, L.nx, L.ny, L.nz), F);
+  else
+    store_odd_pair<D, PARITY>(f, plane, odd_pair(x0, y, z, L.nx, L.ny, L.nz), x0 + 1 < L.nx, F);
 }
 
+// Pair slot first + threadIdx.x of tile [first, end) of lattice L.
 template <int PARITY, bool SHEAR>
 __device__ __forceinline__ void batch_tile(const BatchLattice &L, const float *rates, uint32_t first, uint32_t end,
                                            uint32_t step_lo, uint32_t step_hi) {
+  const uint32_t slot = first + threadIdx.x;
+  if (slot >= end) return;
   if (L.D == 3) {
     if (L.nx % 2 == 0)
-      batch_sites<3, PARITY, SHEAR, true>(L, rates, first, end, step_lo, step_hi);
+      batch_sites<3, PARITY, SHEAR, true>(L, rates, slot, step_lo, step_hi);
     else
-      batch_sites<3, PARITY, SHEAR, false>(L, rates, first, end, step_lo, step_hi);
+      batch_sites<3, PARITY, SHEAR, false>(L, rates, slot, step_lo, step_hi);
   } else {
     if (L.nx % 2 == 0)
-      batch_sites<2, PARITY, SHEAR, true>(L, rates, first, end, step_lo, step_hi);
+      batch_sites<2, PARITY, SHEAR, true>(L, rates, slot, step_lo, step_hi);
     else
-      batch_sites<2, PARITY, SHEAR, false>(L, rates, first, end, step_lo, step_hi);
+      batch_sites<2, PARITY, SHEAR, false>(L, rates, slot, step_lo, step_hi);
   }
 }
 
@@ -183,8 +260,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) batch_kernel(const BatchA
     }
     __syncthreads();
     if (!s_ok) break;
-    const uint32_t first = (uint32_t)(t - L.tile0) * (uint32_t)a.span;
-    const uint32_t end = first + (uint32_t)a.span < L.plane ? first + (uint32_t)a.span : L.plane;
+    const uint32_t first = (uint32_t)(t - L.tile0) * (uint32_t)a.tile_slots;
+    const uint32_t slots = pair_slots(L);
+    const uint32_t end = first + (uint32_t)a.tile_slots < slots ? first + (uint32_t)a.tile_slots : slots;
     const unsigned long long step = (unsigned long long)(step0 + s);
     const uint32_t lo = (uint32_t)step, hi = (uint32_t)(step >> 32);
     if (step & 1)
@@ -222,14 +300,17 @@ __global__ void __launch_bounds__(MINB >= 5 ? 128 : kBatchMaxThreads, MINB)
   const int t = tile_base + (int)blockIdx.x;
   const int lat = lattice_of(a, t, lat_lo, lat_hi);
   const BatchLattice &L = a.lats[lat];
-  const uint32_t first = (uint32_t)(t - L.tile0) * (uint32_t)a.span;
-  const uint32_t end = first + (uint32_t)a.span < L.plane ? first + (uint32_t)a.span : L.plane;
+  const uint32_t first = (uint32_t)(t - L.tile0) * (uint32_t)a.tile_slots;
+  const uint32_t slots = pair_slots(L);
+  const uint32_t end = first + (uint32_t)a.tile_slots < slots ? first + (uint32_t)a.tile_slots : slots;
+  const uint32_t slot = first + threadIdx.x;
+  if (slot >= end) return;
   const unsigned long long step = (unsigned long long)(*a.step_counter + k);
   const float *rates = a.rates + 54 * lat;
   if (L.nx % 2 == 0)
-    batch_sites<D, PARITY, SHEAR, true, ROLLED>(L, rates, first, end, (uint32_t)step, (uint32_t)(step >> 32));
+    batch_sites<D, PARITY, SHEAR, true, ROLLED>(L, rates, slot, (uint32_t)step, (uint32_t)(step >> 32));
   else
-    batch_sites<D, PARITY, SHEAR, false, ROLLED>(L, rates, first, end, (uint32_t)step, (uint32_t)(step >> 32));
+    batch_sites<D, PARITY, SHEAR, false, ROLLED>(L, rates, slot, (uint32_t)step, (uint32_t)(step >> 32));
 }
 
 // Advances the shared step counter after the n step launches of one call.

@@ -45,7 +45,7 @@ struct BatchLattice {  // one lattice of a batch (FP32 storage); lives in the ke
 struct BatchArgs {
   const float *rates;        // general rates: om[27] then phc[27] per lattice (device)
   int nlat, ntiles, nsteps;  // lattices, tiles (all lattices), steps of this launch
-  int span;                  // sites per tile (2 * threads per block)
+  int tile_slots;            // pair slots (two x-adjacent sites) per tile = threads per block
   long long *step_counter;   // device: completed steps of every lattice
   int *done;                 // device, one per lattice, zero at launch: tiles finished
   unsigned int *exits;       // device, zero at launch: blocks that have left

@@ -63,6 +63,10 @@ def _specs(general=False):
         dict(lattice=0, dims=(33, 17, 1), lam=_lam(0, 0.7), kBT=1e-5, rho0=1.3, seed=14),
         dict(lattice=1, dims=(2, 3, 1), lam=_lam(1, 1.2), kBT=2e-4, rho0=1.0, seed=(1 << 40) + 15),
         dict(lattice=0, dims=(600, 3, 1), lam=_lam(0, 1.98), kBT=1e-4, rho0=1.0, seed=16),
+        # rows of one and three sites: every pair slot of a row is the lone last one, or
+        # one pair and one lone site
+        dict(lattice=1, dims=(1, 5, 3), lam=_lam(1, 1.4), kBT=1e-4, rho0=1.0, seed=17),
+        dict(lattice=0, dims=(3, 7, 1), lam=_lam(0, 1.1), kBT=2e-4, rho0=1.0, seed=18),
     ]
     if general:
         s[0]["lam"] = _general(1, 21)
@@ -71,7 +75,7 @@ def _specs(general=False):
 
 
 _U0 = [(0.05, 0.02, 0.0), (-0.03, 0.01, 0.02), (0.04, -0.02, 0.0), (0.0, 0.03, 0.0),
-       (0.01, 0.01, 0.01), (-0.05, 0.0, 0.0)]
+       (0.01, 0.01, 0.01), (-0.05, 0.0, 0.0), (0.02, -0.01, 0.03), (-0.02, 0.04, 0.0)]
 
 
 def _init(batch):
