@@ -268,3 +268,42 @@ def test_persistent_wait_timeout_reported_and_recoverable(fl):
         assert np.array_equal(x, y)
     for x, y in zip(got, ref):
         assert np.array_equal(x, y)
+
+
+def test_batch_at_the_lattice_limit(fl, oracle_mod):
+    # FLBM_BATCH_MAX_LATTICES lattices (the by-value table of the kernel arguments is
+    # full), mixed types, sizes and parities, every launch form; one more is refused.
+    n = fl.FLBM_BATCH_MAX_LATTICES
+    rng = np.random.default_rng(7)
+    specs = []
+    for j in range(n):
+        if j % 2:
+            dims = tuple(int(v) for v in rng.integers(1, 6, 3))
+            specs.append(dict(lattice=1, dims=dims, lam=_lam(1, 1.0 + 0.9 * rng.random()), kBT=1e-4, rho0=1.0,
+                              seed=5000 + j))
+        else:
+            dims = (int(rng.integers(1, 12)), int(rng.integers(1, 9)), 1)
+            specs.append(dict(lattice=0, dims=dims, lam=_lam(0, 1.0 + 0.9 * rng.random()), kBT=1e-4, rho0=1.0,
+                              seed=5000 + j))
+    with pytest.raises(fl.FlbmError) as e:
+        fl.Batch(specs + [specs[0]])
+    assert e.value.status == fl.FLBM_EINVAL
+    results = []
+    for form in (0, 1, 2, 3):
+        with fl.Batch(specs) as b:
+            b.shape = (64 if form != 1 else 128, form)
+            f0 = []
+            for i in range(n):
+                b.lattice(i).init_uniform((0.02, -0.01, 0.01), 1e-3, i)
+                if i in (0, 1, n - 2, n - 1):
+                    f0.append(b.lattice(i).populations())
+            b.step(4)
+            b.sync()
+            results.append([b.lattice(i).populations() for i in (0, 1, n - 2, n - 1)])
+    for r in results[1:]:
+        for x, y in zip(r, results[0]):
+            assert np.array_equal(x, y)
+    for k, i in enumerate((0, 1, n - 2, n - 1)):
+        d = specs[i]
+        fo = oracle_mod.run(d["lattice"], d["dims"], d["lam"], d["kBT"], d["seed"], f0[k], 0, 4)
+        assert _err(results[0][k], fo, d["lattice"], d["rho0"]) <= TOL, i
