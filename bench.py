@@ -494,14 +494,17 @@ def run_reference(args):
     f = oracle.init_uniform(1, dims, 1.0, U0, AMP, SEED)
     for k in range(args.warmup):
         f = oracle.run(1, dims, lam, KBT, SEED, f, k, 1, threads=threads)
+    S = args.stats_every
     t = time.perf_counter()
     for k in range(args.steps):
+        if k % S == 0:  # the statistics of the state the step reads, as in the GPU arm
+            oracle.stats(1, dims, f)
         f = oracle.run(1, dims, lam, KBT, SEED, f, args.warmup + k, 1, threads=threads)
     dt = time.perf_counter() - t
     sites = int(np.prod(dims))
     value = sites * args.steps / dt / 1e9
     sample = (f"D3Q27 {dims[0]}x{dims[1]}x{dims[2]} per step (bounded sample of the 256^3 workload, "
-              "same physics), FP64 oracle, OpenMP over sites")
+              f"same physics, statistics every {S} steps), FP64 oracle, OpenMP over sites")
     return {
         "impl": "reference",
         "metric": METRIC,
@@ -516,7 +519,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded lattice state, no dataset)",
-        "config": workload_config(1, world),
+        "config": workload_config(S, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
