@@ -74,9 +74,10 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
-// D (16x8, FP32) += A (16x8, TF32, row-major) * B (8x8, TF32, column-major).
+// D (16x8, FP32) += A (16x8, TF32, row-major) * B (8x8, TF32, column-major). Not
+// volatile: the compiler may interleave independent accumulations.
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
       "{%0, %1, %2, %3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -243,13 +244,14 @@ struct Warp {
         bl[nt][0] = al[mt][h];
         bl[nt][1] = al[mt][h + 2];
       }
+      // hi*hi, then hi*lo, then lo*hi over all tiles: consecutive MMAs go to different
+      // accumulators, so none waits for the one before it.
 #pragma unroll
-      for (int i = 0; i < P::NTILE; ++i) {
-        const int mt = tile_mt<D>(i), nt = tile_nt<D>(i);
-        mma_tf32(d[i], ah[mt], bh[nt]);
-        mma_tf32(d[i], ah[mt], bl[nt]);
-        mma_tf32(d[i], al[mt], bh[nt]);
-      }
+      for (int i = 0; i < P::NTILE; ++i) mma_tf32(d[i], ah[tile_mt<D>(i)], bh[tile_nt<D>(i)]);
+#pragma unroll
+      for (int i = 0; i < P::NTILE; ++i) mma_tf32(d[i], ah[tile_mt<D>(i)], bl[tile_nt<D>(i)]);
+#pragma unroll
+      for (int i = 0; i < P::NTILE; ++i) mma_tf32(d[i], al[tile_mt<D>(i)], bh[tile_nt<D>(i)]);
     }
   }
 
