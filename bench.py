@@ -525,6 +525,42 @@ def run_reference(args):
     }
 
 
+def run_profile_workload(args):
+    """A short run of one kernel family for ncu captures (no timing, no bench line):
+    stats: a D3Q27 box of --dims, two steps, two statistics reductions; d3q19: a D3Q19 box
+    of --dims with the paper's rates (shear 1.6), four steps of --variant (default 2);
+    batch: the 256-lattice ensemble, three steps of the per-step five-blocks form."""
+    import torch
+
+    import paper_2602_16486_gb300 as fl
+
+    torch.cuda.set_device(0)
+    dims = tuple(args.dims)
+    if args.profile == "stats":
+        with fl.Lattice(fl.FLBM_D3Q27, dims, lam_d3q27(), KBT, 1.0, SEED) as lat:
+            lat.init_uniform(U0, AMP, SEED)
+            lat.step(2)
+            lat.stats()
+            lat.stats()
+    elif args.profile == "d3q19":
+        lam = np.ones(19)
+        lam[[7, 8, 9]] = OMEGA
+        with fl.Lattice(fl.FLBM_D3Q19, dims, lam, KBT, 1.0, SEED) as lat:
+            lat.variant = args.variant or 2
+            lat.init_uniform(U0, AMP, SEED)
+            lat.step(4)
+            lat.sync()
+    else:
+        specs = draw_ensemble()
+        with fl.Batch(specs) as b:
+            for i in range(len(specs)):
+                b.lattice(i).init_uniform((0.0, 0.0, 0.0), 0.0, 0)
+            b.shape = (128, 2)
+            b.step(3)
+            b.sync()
+    return {"profile": args.profile, "dims": list(dims), "note": "profiling workload: not a bench line"}
+
+
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
@@ -542,7 +578,12 @@ def main(argv=None):
                    help="step-kernel variant (1-6); default 0 = autotune")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the 16-bit storage and batched-ensemble measurements")
+    p.add_argument("--profile", choices=["stats", "d3q19", "batch"], default=None,
+                   help="run a short workload of one kernel family for ncu captures and exit")
     args = p.parse_args(argv)
+    if args.profile:
+        print(json.dumps(run_profile_workload(args)), flush=True)
+        return
     if args.warmup < 3:
         p.error("--warmup must be >= 3")
     world, _, _ = dist_setup()
