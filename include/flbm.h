@@ -309,8 +309,8 @@ int64_t flbm_batch_get_step(const flbm_batch *b);
  * 2 * threads sites; 0 = the default, 128) and the form:
  *   0 per-step launches, up to 128 registers, D3Q27 noise loop unrolled (default);
  *   1 persistent cooperative launch (rolled noise loop, both lattice types in one kernel);
- *   2 per-step launches compiled for five resident blocks per SM (up to 102 registers;
- *     threads <= 128);
+ *   2 per-step launches compiled for more resident blocks per SM: five for D3Q27 (up
+ *     to 102 registers), ten for D2Q9 (up to 51); threads <= 128;
  *   3 per-step launches, up to 128 registers, D3Q27 noise loop rolled (smaller code).
  * flbm_batch_autotune times every (form, threads) pair over trial_steps steps (rounded
  * up to even) on a copy of the state (restored afterwards, step count unchanged), keeps

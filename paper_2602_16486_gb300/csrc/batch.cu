@@ -324,13 +324,15 @@ cudaError_t batch_max_blocks(bool shear, int threads, int *blocks_per_sm) {
 }
 
 // Launch shapes of the per-step form (BatchForm): register cap 128 (up to 256 threads,
-// two blocks per SM) or 102 (up to 128 threads, five blocks per SM), D3Q27 noise loop
-// unrolled or rolled (D2Q9 has no loop).
+// two blocks per SM), or up to 128 threads with five (D3Q27, 102 registers) or ten (D2Q9,
+// 51 registers: its lighter update gains from the extra warps) blocks per SM; D3Q27
+// noise loop unrolled or rolled (D2Q9 has no loop).
 template <int D, bool SHEAR, int PARITY>
 cudaError_t launch_group(int form, const BatchArgs &a, int k, const BatchGroup &g, int threads, cudaStream_t s) {
   if (g.ntiles <= 0) return cudaSuccess;
-  if (form == kBatchStepOcc)
-    batch_step_kernel<D, SHEAR, PARITY, false, 5><<<g.ntiles, threads, 0, s>>>(a, k, g.lat_lo, g.lat_hi, g.tile0);
+  if (form == kBatchStepOcc)  // D3Q27: five blocks per SM; the lighter D2Q9 update: ten
+    batch_step_kernel<D, SHEAR, PARITY, false, D == 3 ? 5 : 10><<<g.ntiles, threads, 0, s>>>(a, k, g.lat_lo,
+                                                                                         g.lat_hi, g.tile0);
   else if (form == kBatchStepRolled)  // D2Q9 has no noise loop: the same kernel as form 0
     batch_step_kernel<D, SHEAR, PARITY, D == 3, 2><<<g.ntiles, threads, 0, s>>>(a, k, g.lat_lo, g.lat_hi, g.tile0);
   else

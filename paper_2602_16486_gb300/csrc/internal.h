@@ -65,7 +65,7 @@ struct BatchGroup {
 enum BatchForm {
   kBatchStep = 0,        // per-step launches, 128-register cap, unrolled D3Q27 noise
   kBatchPersistent = 1,  // one cooperative launch, per-lattice completion counters
-  kBatchStepOcc = 2,     // per-step launches, 102-register cap (five blocks of <= 128)
+  kBatchStepOcc = 2,     // per-step launches, five (D3Q27) / ten (D2Q9) blocks of <= 128 per SM
   kBatchStepRolled = 3,  // per-step launches, 128-register cap, rolled D3Q27 noise
   kBatchFormMax = 3
 };
