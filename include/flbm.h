@@ -219,9 +219,10 @@ int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storage, int pari
  * (smaller code), 4 = a persistent kernel that prefetches each row's populations into
  * shared memory with bulk asynchronous copies (needs nx even, nx <= 512 and a
  * population row a multiple of 16 bytes; else it falls back to 2), 5 and 6 = 2 and 3
- * compiled for five resident blocks per SM (at most 102 registers, more warps to hide
- * latency; for D2Q9 they are 2 and 3). Variants 2-6 fall back to 1 when nx is odd. The environment variable FLBM_STEP_VARIANT, read by
- * flbm_create, sets the initial choice.
+ * compiled for more resident blocks per SM to hide latency: five for the 3-D lattices
+ * (at most 102 registers), ten for D2Q9 (at most 51). Variants 2-6 fall back to 1 when
+ * nx is odd. The environment variable FLBM_STEP_VARIANT, read by flbm_create, sets the
+ * initial choice.
  * flbm_autotune times every applicable variant over trial_steps steps on a copy of the
  * current state (restored afterwards: populations and step count are unchanged), keeps
  * the fastest for this context and caches the choice per (GPU model, lattice, storage,

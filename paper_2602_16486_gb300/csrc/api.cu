@@ -681,7 +681,6 @@ int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
     const int candidates[6] = {kStepOneSite, kStepPair, kStepPairRolled, kStepPipelined, kStepPairOcc,
                                kStepPairRolledOcc};
     for (int v : candidates) {
-      if ((v == kStepPairOcc || v == kStepPairRolledOcc) && c->D != 3) continue;  // same as 2 and 3
       if (pair_variants_only(c->lattice) &&
           (v == kStepPairRolled || v == kStepPipelined || v == kStepPairRolledOcc))
         continue;

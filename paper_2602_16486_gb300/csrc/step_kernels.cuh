@@ -55,10 +55,10 @@ template <int D, typename S, int PARITY, bool NOISE, bool SHEAR, bool ISO>
 cudaError_t launch_kernel(int variant, const StepArgs &a, cudaStream_t s) {
   const dim3 block(kStepBlock);
   if (variant != kStepOneSite) {
-    // Register caps: 128 (four blocks of 128 threads per SM) or, for D3Q27, 102 (five
-    // blocks: more warps to hide latency, at the risk of spills). D2Q9 needs fewer than
-    // 102 registers either way, so its variants 5 and 6 are 2 and 3.
-    constexpr int kOcc = D == 3 ? 5 : 4;
+    // Register caps: 128 (four blocks of 128 threads per SM) or, for variants 5 and 6,
+    // 102 for D3Q27 (five blocks: more warps to hide latency, at the risk of spills) and
+    // 51 for the lighter D2Q9 update (ten blocks).
+    constexpr int kOcc = D == 3 ? 5 : 10;
     const dim3 grid((a.nx / 2 + kStepBlock - 1) / kStepBlock, a.ny, a.nz);
     const bool occ = variant == kStepPairOcc || variant == kStepPairRolledOcc;
     const bool rolled = !ISO && (variant == kStepPairRolled || variant == kStepPairRolledOcc);
