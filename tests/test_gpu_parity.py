@@ -94,7 +94,7 @@ def test_d3q27_general_rates(fl, oracle_mod):
     assert _err(fg, fo, 1) <= TOL
 
 
-@pytest.mark.parametrize("variant", [1, 3, 4])
+@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6])
 def test_d2q9_paper_rates(fl, oracle_mod, variant):
     # D2Q9 with the paper's rates (L_4 = L_5 = omega, every other mode 1): the
     # specialised path that forms only the shear central moments.
@@ -104,7 +104,7 @@ def test_d2q9_paper_rates(fl, oracle_mod, variant):
     assert _err(fg, fo, 0) <= TOL
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
 def test_d2q9_general_rates_ragged(fl, oracle_mod, variant):
     rng = np.random.default_rng(6)
     lam = np.ones(9)
