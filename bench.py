@@ -334,6 +334,7 @@ def run_ours(args):
     }
     if world == 1 and not args.no_extras:
         line["storage_widths"] = storage_widths(fl, torch, stream, dims, peaks["hbm_gbs"])
+        line["other_lattices"] = other_lattices(fl, torch, stream, dims, peaks["hbm_gbs"])
         line["batched_ensemble"] = batched_ensemble(fl, torch, peaks["hbm_gbs"])
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
@@ -390,6 +391,28 @@ def storage_widths(fl, torch, stream, dims, peak):
             out[name] = {"value": round(sites / (ms * 1e-3) / 1e9, 3), "unit": UNIT, "ms_per_step": round(ms, 5),
                          "step_variant": variant, "achieved_gbs": round(gbs, 1),
                          "frac_of_hbm": round(gbs / peak, 4), "bytes_per_site": 108}
+    return out
+
+
+def other_lattices(fl, torch, stream, dims, peak):
+    """GLUPS of the same workload (drift, perturbation, kBT, shear rate 1.6) on the
+    isotropic D3Q27 variant (deviators at the shear rate too) and on D3Q19, FP32."""
+    out = {}
+    sites = dims[0] * dims[1] * dims[2]
+    lam_iso = np.ones(27)
+    lam_iso[[5, 6, 7, 8, 9]] = OMEGA
+    lam19 = np.ones(19)
+    lam19[[7, 8, 9]] = OMEGA
+    for lattice, lam, q, name in ((fl.FLBM_D3Q27_ISO, lam_iso, 27, "d3q27_isotropic"), (fl.FLBM_D3Q19, lam19, 19, "d3q19")):
+        with fl.Lattice(lattice, dims, lam, KBT, 1.0, SEED, cuda_stream=stream.cuda_stream) as lat:
+            lat.init_uniform(U0, AMP, SEED)
+            variant = lat.autotune(10)
+            lat.step(6)
+            ms = _event_time(torch, stream, lat.step, 200)
+            gbs = q * 4 * 2 * sites / (ms * 1e-3) / 1e9
+            out[name] = {"value": round(sites / (ms * 1e-3) / 1e9, 3), "unit": UNIT, "ms_per_step": round(ms, 5),
+                         "step_variant": variant, "achieved_gbs": round(gbs, 1),
+                         "frac_of_hbm": round(gbs / peak, 4), "bytes_per_site": q * 8}
     return out
 
 
@@ -577,7 +600,7 @@ def main(argv=None):
     p.add_argument("--variant", type=int, default=0,
                    help="step-kernel variant (1-6); default 0 = autotune")
     p.add_argument("--no-extras", action="store_true",
-                   help="skip the 16-bit storage and batched-ensemble measurements")
+                   help="skip the 16-bit storage, other-lattice and batched-ensemble measurements")
     p.add_argument("--profile", choices=["stats", "d3q19", "batch"], default=None,
                    help="run a short workload of one kernel family for ncu captures and exit")
     args = p.parse_args(argv)
