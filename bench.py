@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fluctuating D3Q27 GLUPS and fraction of HBM roofline at stated oracle error"
 UNIT = "GLUPS"
 DIMS = (256, 256, 256)  # overridable with --dims for profiling runs on smaller boxes
+STATS_RECORD_BYTES = (32 * 33 // 2 + 1) * 8  # one D3Q27 statistics record on the device
 KBT = 1e-4
 OMEGA = 1.6
 U0 = (0.05, 0.02, 0.0)
@@ -267,7 +268,6 @@ def run_ours(args):
     host_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     fl.flbm_save(lat.ctx, host_in.data_ptr(), nbytes)
     n_e2e = args.steps
-    stats_bytes = 0
     barrier()
     torch.cuda.synchronize()
     w0 = time.perf_counter()
@@ -275,8 +275,9 @@ def run_ours(args):
     for k in range(n_e2e):
         lat.step(1)
         if k % S == 0:
-            lat.stats()
-            stats_bytes += (14 + 27 + 27 * 28 // 2 + 1) * 8
+            lat.sample()
+    e2e_samples = lat.fetch_samples()  # every sample's record to the host
+    stats_bytes = len(e2e_samples) * STATS_RECORD_BYTES
     fl.flbm_save(lat.ctx, host_out.data_ptr(), nbytes)
     e2e_s = time.perf_counter() - w0
     e2e_s = max_over_ranks(e2e_s, world, "cuda")
@@ -325,8 +326,9 @@ def run_ours(args):
             "unit": UNIT,
             "h2d_bytes_per_step": int(nbytes / n_e2e),
             "d2h_bytes_per_step": int((nbytes + stats_bytes) / n_e2e),
-            "what": "flbm_load from pinned host blob, K x flbm_step(1) with flbm_stats every "
-                    f"{S} steps (sync + D2H), flbm_save to pinned host; wall clock",
+            "what": "flbm_load from pinned host blob, K x flbm_step(1) with flbm_sample every "
+                    f"{S} steps, flbm_fetch_samples (D2H of every record), flbm_save to pinned host; "
+                    "wall clock",
         },
         "gpu_launches": launches,
         "clocks": clocks.summary(),
