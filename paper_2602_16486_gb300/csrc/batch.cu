@@ -1,34 +1,36 @@
 // Batched ensembles: many independent periodic lattices (mixed D2Q9 / D3Q27, own size,
-// rates, kBT and noise seed) advanced by one persistent kernel.
+// rates, kBT and noise seed) advanced together, each by exactly the fused update of a
+// single context (the collision of collide.cuh, packed FP32x2, the AA pattern of step.cu)
+// with its own parameters.
 //
 // The host lays every lattice's populations out in one allocation and cuts all lattices
 // into tiles of equal pair-slot count (one slot of two x-adjacent sites per thread; a
-// tile may span rows, never lattices). One cooperative launch runs n steps: block b takes the work items
-// (step s, tile b + j G) in step-major order, and applies to each the same fused update
-// as the single-lattice kernels (collide.cuh: rolled noise loop, packed FP32x2, the AA
-// pattern of step.cu) with that lattice's parameters.
+// tile may span rows, never lattices). Two launch structures (BatchForm):
 //
-// There is no grid-wide barrier between steps. Lattices are independent, so a tile of
-// lattice L at step s only has to wait until every tile of L has finished step s - 1
-// (in-place AA streaming reads and writes neighbour slots across tile boundaries). Each
-// lattice has a completion counter; a block announces a finished tile with a release
-// (fence, then atomic add) and checks the counter of the next tile's lattice with an
-// acquire before starting it. Blocks run ahead into the next step on lattices that are
-// done, so the per-step tail of the slowest block no longer idles the machine. Progress
-// is guaranteed: all blocks are resident (cooperative launch), each walks its items in
+// Per-step forms (the default): per step one plain launch per lattice type, block b on
+// tile tile0 + b, the hardware block scheduler balancing the load; the n launches of a
+// call are captured once into a CUDA graph and replayed.
+//
+// Persistent form: one cooperative launch runs n steps; block b takes the work items
+// (step s, tile b + j G) in step-major order. There is no grid-wide barrier between
+// steps. Lattices are independent, so a tile of lattice L at step s only has to wait
+// until every tile of L has finished step s - 1 (in-place AA streaming reads and writes
+// neighbour slots across tile boundaries). Each lattice has a completion counter; a block
+// announces a finished tile with a release (fence, then atomic add) and checks the
+// counter of the next tile's lattice with an acquire before starting it. Progress is
+// guaranteed: all blocks are resident (cooperative launch), each walks its items in
 // order, and the lowest pending item only depends on items of the step before it, which
-// are all complete.
+// are all complete. Every wait is bounded: a block that polls longer than wait_polls times
+// (or sees another block's failure) sets the status word and leaves; the host reports
+// FLBM_ETIMEOUT.
 //
 // The per-lattice parameters travel by value in the kernel arguments (constant bank; at
-// most kBatchMaxLattices lattices). A tile's lattice is found by a binary search over
-// the lattices' first-tile indices in that table, from the block's own counters only,
-// so the lattice's parameters stay block-uniform values (uniform registers) instead of
-// occupying every thread's registers. All lattices share the step counter in device memory: read at entry and
-// advanced by the last block to leave, so that one captured graph of the launch serves
-// every call with the same n.
-//
-// Every wait is bounded: a block that polls longer than wait_polls times (or sees another
-// block's failure) sets the status word and leaves; the host reports FLBM_ETIMEOUT.
+// most kBatchMaxLattices lattices). A tile's lattice is found by a binary search over the
+// lattices' first-tile indices in that table, from the block's own counters only, so the
+// lattice's parameters stay block-uniform values (uniform registers) instead of occupying
+// every thread's registers. All lattices share the step counter in device memory, read
+// by every launch, so that one captured graph serves every call with the same n (and,
+// for the per-step forms, the same starting parity).
 #include <cuda_runtime.h>
 
 #include "collide.cuh"
