@@ -1,6 +1,9 @@
 // C ABI of the library (declared and documented in include/flbm.h): argument checks,
-// context ownership, launch sequencing and host <-> device exchange. Every compute
-// step runs in the kernels of step.cu, stats.cu and state.cu.
+// context and batch ownership, launch sequencing, graph capture of batch steps, the
+// autotuners and host <-> device exchange. Every compute step runs in the kernels of the
+// other translation units: the step (step.cu, step_16.cu, step_iso.cu, step19.cu,
+// step_pipe.cu), the statistics (stats.cu), initialisation and exchange (state.cu) and
+// batches (batch.cu).
 #include <cuda_runtime.h>
 
 #include <cmath>
