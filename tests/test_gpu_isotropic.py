@@ -96,3 +96,23 @@ def test_iso_rejected_in_batches(fl):
     with pytest.raises(fl.FlbmError) as e:
         fl.Batch([dict(lattice=ISO, dims=(8, 8, 8), lam=lam, kBT=1e-4, rho0=1.0, seed=0)])
     assert e.value.status == fl.FLBM_EINVAL
+
+
+@pytest.mark.parametrize("storage,bits", [(1, 8), (2, 11)])
+@pytest.mark.parametrize("dims", [(20, 7, 6), (13, 6, 5)])
+def test_iso_reduced_precision_one_step_bound(fl, oracle_mod, storage, bits, dims):
+    # One update from the stored state: the only error beyond FP32 arithmetic is the
+    # rounding of each stored deviation d* to the format (relative 2^-bits).
+    lam = np.ones(27)
+    lam[5:10] = 1.6
+    with fl.Lattice(ISO, dims, lam, 1e-4, 1.0, 5, storage) as lat:
+        lat.init_uniform((0.02, -0.01, 0.01), 1e-3, 2)
+        lat.step(3)
+        f0 = lat.populations()
+        lat.step(1)
+        fg = lat.populations()
+    fo = oracle_mod.run(ISO, dims, lam, 1e-4, 5, f0, 3, 1)
+    dev = np.abs(fo - _w())
+    # 3e-8 covers the absolute spacing of FP16 subnormals (2^-24) below 6.1e-5.
+    assert np.all(np.abs(fg - fo) <= dev * 2.0 ** -bits * 1.01 + 2e-6 * np.abs(fo) + 3e-8), \
+        float((np.abs(fg - fo) / (dev * 2.0 ** -bits + 1e-30)).max())
