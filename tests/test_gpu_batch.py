@@ -307,3 +307,29 @@ def test_batch_at_the_lattice_limit(fl, oracle_mod):
         d = specs[i]
         fo = oracle_mod.run(d["lattice"], d["dims"], d["lam"], d["kBT"], d["seed"], f0[k], 0, 4)
         assert _err(results[0][k], fo, d["lattice"], d["rho0"]) <= TOL, i
+
+
+def test_batch_zero_temperature_members(fl, oracle_mod):
+    # kBT = 0 (Test 1 of the paper): the batch kernels still draw the normals but scale
+    # them by zero, so a member at rest stays exactly at rest and a drifting member follows
+    # the deterministic oracle; a noisy member beside them is unaffected.
+    specs = [
+        dict(lattice=1, dims=(10, 6, 5), lam=_lam(1, 1.5), kBT=0.0, rho0=1.0, seed=1),
+        dict(lattice=0, dims=(31, 12, 1), lam=_lam(0, 1.7), kBT=0.0, rho0=1.2, seed=2),
+        dict(lattice=1, dims=(9, 7, 4), lam=_lam(1, 1.3), kBT=0.0, rho0=1.0, seed=3),
+        dict(lattice=0, dims=(16, 10, 1), lam=_lam(0, 1.2), kBT=1e-4, rho0=1.0, seed=4),
+    ]
+    with fl.Batch(specs) as b:
+        b.lattice(0).init_uniform((0.0, 0.0, 0.0), 0.0, 0)
+        b.lattice(1).init_uniform((0.0, 0.0, 0.0), 0.0, 0)
+        b.lattice(2).init_uniform((0.03, -0.02, 0.01), 1e-3, 5)
+        b.lattice(3).init_uniform((0.0, 0.0, 0.0), 1e-3, 6)
+        f0 = [b.lattice(i).populations() for i in range(len(specs))]
+        b.step(12)
+        got = [b.lattice(i).populations() for i in range(len(specs))]
+    for i in (0, 1):
+        assert np.array_equal(got[i], f0[i]), i
+    for i in (2, 3):
+        d = specs[i]
+        fo = oracle_mod.run(d["lattice"], d["dims"], d["lam"], d["kBT"], d["seed"], f0[i], 0, 12)
+        assert _err(got[i], fo, d["lattice"], d["rho0"]) <= TOL, i
