@@ -187,26 +187,29 @@ int flbm_load(flbm_ctx *ctx, const void *host, size_t bytes);
  * flbm_stats_noalloc - the statistics of flbm_stats (same kernel, same flbm_stats_t)
  * for a population array the caller owns, with no allocation of any kind. The paper
  * has no counterpart: this entry point exists for callers that cannot allocate GPU
- * memory - code that owns the whole device-memory budget through its own pool, code
- * that must not change its memory footprint once running, or code inside a CUDA stream
- * capture, where cudaMalloc is not allowed. flbm_create cannot serve them, because it
- * allocates its buffers.
+ * memory - an application whose own memory pool owns the whole device-memory budget
+ * (a cudaMalloc from elsewhere would fail or break its accounting), or a service that
+ * must not change its memory footprint once running. flbm_create cannot serve them,
+ * because it allocates its buffers.
  *   lattice, dims, storage, rho0 : as given to flbm_create_ex for this array.
  *   parity          : completed steps mod 2 (flbm_get_step(ctx) & 1): 0 when the array
  *                     holds f_i(x) in slot i at x, 1 after an odd number of AA steps.
  *   dev_populations : the stored deviations, device memory, Q * sites elements of the
- *                     storage type (e.g. the dev_buf handed to flbm_create_ex).
- *   cuda_stream     : stream to run on (NULL = legacy default stream); synchronised.
+ *                     storage type (e.g. the dev_buf handed to flbm_create_ex), 256-byte
+ *                     aligned like dev_buf (the kernel reads element pairs); any other
+ *                     address is rejected with FLBM_EINVAL before device work.
+ *   cuda_stream     : stream to run on (NULL = legacy default stream). The call waits
+ *                     for this stream before it returns.
  *   out             : host struct, written on FLBM_OK and FLBM_ENUMERIC; out->step is
  *                     -1 (the array carries no step count).
  * Scratch: the FP64 accumulators live in one statically allocated device array of
  * FLBM_NOALLOC_SCRATCH_DOUBLES doubles (8 KiB), which every GPU that loads the library
  * keeps until the process exits. A lattice whose accumulators would not fit is rejected
- * with FLBM_EINVAL (D2Q9 needs 137 doubles, D3Q27 529). The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) and caches it; make that first
- * call before any stream capture. Every call reuses the same array and zeroes it first,
- * so calls whose GPU work overlaps (other streams, other host threads) race and return
- * wrong sums: serialise them.
+ * with FLBM_EINVAL (D2Q9 needs 137 doubles, D3Q27 and D3Q19 529). The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and caches it; make
+ * that first call before any stream capture. Every call reuses the same array and zeroes
+ * it first, so calls whose GPU work overlaps (other streams, other host threads) race
+ * and return wrong sums: serialise them.
  */
 #define FLBM_NOALLOC_SCRATCH_DOUBLES 1024
 int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storage, int parity, double rho0,
@@ -288,6 +291,18 @@ int flbm_batch_size(const flbm_batch *b);
  * all of its lattices together), and flbm_destroy ignores it.
  */
 flbm_ctx *flbm_batch_lattice(flbm_batch *b, int i);
+
+/*
+ * flbm_batch_stats - the statistics of lattice i of the batch, exactly as flbm_stats on
+ * flbm_batch_lattice(b, i): velocity moments (Sec. III, <u_a^2>) and central-moment means
+ * and raw second moments (Sec. II-B, C^eq) of one member of the ensemble; the paper gathers
+ * its fluctuation statistics over such ensembles of independent runs (Sec. III).
+ *   i   : 0 <= i < flbm_batch_size(b), else FLBM_EINVAL.
+ *   out : host struct; written on FLBM_OK and on FLBM_ENUMERIC (some site not finite).
+ * Waits for the batch's stream (the statistics of the state after every step enqueued
+ * so far).
+ */
+int flbm_batch_stats(flbm_batch *b, int i, flbm_stats_t *out);
 
 /*
  * flbm_batch_step - enqueue n >= 0 steps of every lattice. Never synchronises. Every

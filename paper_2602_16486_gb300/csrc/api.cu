@@ -1046,6 +1046,14 @@ flbm_ctx *flbm_batch_lattice(flbm_batch *b, int i) {
   return b->members[size_t(i)];
 }
 
+int flbm_batch_stats(flbm_batch *b, int i, flbm_stats_t *out) {
+  if (!b) return fail(FLBM_EINVAL, "batch is NULL");
+  if (i < 0 || i >= int(b->members.size()))
+    return fail(FLBM_EINVAL, "no lattice %d in this batch of %d", i, int(b->members.size()));
+  if (!out) return fail(FLBM_EINVAL, "out is NULL");
+  return flbm_stats(b->members[size_t(i)], out);
+}
+
 int flbm_batch_step(flbm_batch *b, int64_t n) {
   if (!b) return fail(FLBM_EINVAL, "batch is NULL");
   if (n < 0 || n > 0x7fffffff) return fail(FLBM_EINVAL, "n = %lld must lie in [0, 2^31)", (long long)n);
@@ -1246,8 +1254,10 @@ extern "C" int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storag
   if (parity != 0 && parity != 1) return fail(FLBM_EINVAL, "parity must be 0 or 1, got %d", parity);
   if (!(rho0 > 0.0) || !std::isfinite(rho0)) return fail(FLBM_EINVAL, "rho0 = %g must be finite and > 0", rho0);
   if (!dev_populations) return fail(FLBM_EINVAL, "dev_populations is NULL");
-  if (reinterpret_cast<uintptr_t>(dev_populations) % storage_bytes(storage) != 0)
-    return fail(FLBM_EINVAL, "dev_populations is not aligned to its element size");
+  // The statistics kernel reads element pairs (8 bytes in FP32) on even-nx lattices, the
+  // same kernels flbm_create_ex feeds from a 256-byte aligned dev_buf: require the same.
+  if (reinterpret_cast<uintptr_t>(dev_populations) % 256 != 0)
+    return fail(FLBM_EINVAL, "dev_populations must be 256-byte aligned");
   if (!out) return fail(FLBM_EINVAL, "out is NULL");
   const int Q = q_of(lattice);
   const int len = stats_record_len(Q);

@@ -116,6 +116,7 @@ def _load():
         "flbm_batch_size": (ctypes.c_int, [vp]),
         "flbm_batch_lattice": (vp, [vp, ctypes.c_int]),
         "flbm_batch_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "flbm_batch_stats": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(flbm_stats_t)]),
         "flbm_batch_get_step": (ctypes.c_int64, [vp]),
         "flbm_batch_set_shape": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
         "flbm_batch_get_shape": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
@@ -357,6 +358,14 @@ def flbm_batch_step(b, n=1):
     _check(_lib.flbm_batch_step(b, int(n)))
 
 
+def flbm_batch_stats(b, i, allow_nonfinite=False):
+    out = flbm_stats_t()
+    st = _lib.flbm_batch_stats(b, int(i), ctypes.byref(out))
+    if not (st == FLBM_ENUMERIC and allow_nonfinite):
+        _check(st)
+    return out.to_dict()
+
+
 def flbm_batch_get_step(b):
     return int(_lib.flbm_batch_get_step(b))
 
@@ -510,6 +519,10 @@ class Batch:
     @property
     def step_count(self):
         return flbm_batch_get_step(self.handle)
+
+    def stats(self, i, allow_nonfinite=False):
+        """Statistics of member i (flbm_batch_stats)."""
+        return flbm_batch_stats(self.handle, i, allow_nonfinite)
 
     @property
     def shape(self):

@@ -30,7 +30,8 @@ def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("flbm_create", "flbm_create_ex", "flbm_step", "flbm_stats", "flbm_destroy",
                      "flbm_init_uniform", "flbm_get_populations", "flbm_set_populations",
-                     "flbm_save", "flbm_load", "flbm_last_error"):
+                     "flbm_save", "flbm_load", "flbm_last_error", "flbm_batch_create",
+                     "flbm_batch_step", "flbm_batch_stats"):
         assert required in names
 
 

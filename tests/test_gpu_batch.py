@@ -216,6 +216,40 @@ def test_batch_member_rules_and_stats(fl, oracle_mod):
             b.lattice(len(specs))
 
 
+def test_batch_stats_of_members_match_oracle(fl, oracle_mod):
+    # flbm_batch_stats(b, i) of a D3Q27 and a D2Q9 member of one mixed batch (even and odd
+    # rows), after an odd and an even number of steps, against the oracle's statistics of
+    # the same populations (Sec. III: statistics over ensembles of runs).
+    specs = _specs(False)
+    with fl.Batch(specs) as b:
+        _init(b)
+        for steps in (5, 2):
+            b.step(steps)
+            for i in (0, 3):
+                d = specs[i]
+                st = b.stats(i)
+                ref = oracle_mod.stats(d["lattice"], d["dims"], b.lattice(i).populations())
+                n = int(np.prod(d["dims"]))
+                assert st["step"] == b.step_count and st["sites"] == n and st["nonfinite"] == 0
+                assert st["mass"] == pytest.approx(ref["mass"], rel=1e-7)
+                u2 = np.abs(ref["uu"][:3]).max()
+                np.testing.assert_allclose(st["mom"], ref["mom"], rtol=1e-5, atol=1e-6 * n)
+                np.testing.assert_allclose(st["u_mean"], ref["u_mean"], rtol=1e-5, atol=1e-5 * np.sqrt(u2))
+                np.testing.assert_allclose(st["uu"], ref["uu"], rtol=1e-5, atol=1e-6 * u2)
+                scale = np.sqrt(np.abs(np.diag(ref["k_cov"])))
+                np.testing.assert_allclose(st["k_mean"], ref["k_mean"], atol=1e-5 * scale.max() + 1e-9)
+                np.testing.assert_allclose(st["k_cov"], ref["k_cov"], rtol=1e-4,
+                                           atol=1e-5 * np.outer(scale, scale).max())
+                # the same record as flbm_stats on the borrowed member handle
+                same = b.lattice(i).stats()
+                np.testing.assert_allclose(same["k_cov"], st["k_cov"], rtol=1e-12,
+                                           atol=1e-12 * np.outer(scale, scale).max())
+        for bad in (-1, len(specs)):
+            with pytest.raises(fl.FlbmError) as e:
+                b.stats(bad)
+            assert e.value.status == fl.FLBM_EINVAL
+
+
 def test_batch_invalid_specs(fl):
     good = _specs(False)[:2]
     bad = [dict(good[0]), dict(good[1])]
