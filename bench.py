@@ -418,10 +418,11 @@ def other_lattices(fl, torch, stream, dims, peak):
     return out
 
 
-def batched_ensemble(fl, torch, peak, steps=200):
+def batched_ensemble(fl, torch, peak, steps=200, calls=25):
     """The batched-ensemble workload in one batch (per-step graph-captured launches or one
     persistent launch, as the autotuner picks) against the same lattices stepped one
-    context at a time."""
+    context at a time. The timed region is the workload's 5000 steps: `calls` calls of
+    `steps` steps, each replaying the same captured graph."""
     specs = draw_ensemble()
     sites = sum(int(np.prod(d["dims"])) for d in specs)
     nbytes = sum(int(np.prod(d["dims"])) * (27 if d["lattice"] else 9) * 8 for d in specs)
@@ -433,9 +434,10 @@ def batched_ensemble(fl, torch, peak, steps=200):
         b.step(steps)  # capture of the timed call's graph
         b.sync()
         t = time.perf_counter()
-        b.step(steps)
+        for _ in range(calls):
+            b.step(steps)
         b.sync()
-        ms = (time.perf_counter() - t) * 1e3 / steps
+        ms = (time.perf_counter() - t) * 1e3 / (steps * calls)
         graph = b.uses_graph
     lats = [fl.Lattice(d["lattice"], d["dims"], d["lam"], d["kBT"], d["rho0"], d["seed"]) for d in specs]
     try:
@@ -460,7 +462,7 @@ def batched_ensemble(fl, torch, peak, steps=200):
                         "tau 0.51..2.0, seeds 1000+j), FP32",
             "lattices": len(specs), "sites": sites, "value": round(sites / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
             "ms_per_step": round(ms, 5), "achieved_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4),
-            "threads": threads, "form": ["per-step launches", "persistent launch", "per-step launches, 5 blocks/SM",
+            "steps": steps * calls, "threads": threads, "form": ["per-step launches", "persistent launch", "per-step launches, 5 blocks/SM",
                                          "per-step launches, rolled noise loop"][form], "graph": graph,
             "single_context_loop_ms_per_step": round(ms_loop, 5),
             "speedup_vs_single_context_loop": round(ms_loop / ms, 3),
@@ -474,29 +476,76 @@ def _oracle_sample_dims(target_sites):
     return (n, n, n)
 
 
-def cpu_baseline(budget_s=15.0):
-    """Time the oracle (as it stands) on a bounded sample of the workload."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+# Lattices the oracle is timed on: the 2-D and 3-D sizes of the statistics ensemble and a
+# 32^3 box (the 256^3 workload itself is far too slow for the dense FP64 oracle).
+CPU_LEGS = ((0, (512, 512, 1)), (1, (32, 32, 32)), (1, (64, 64, 64)))
+
+
+def _lam_for(lattice):
+    if lattice == 0:
+        lam = np.ones(9)
+        lam[[4, 5]] = OMEGA
+        return lam
+    return lam_d3q27()
+
+
+def cpu_baseline(budget_s=20.0):
+    """Time the oracle (as it stands) on bounded samples: D2Q9 512^2 and D3Q27 32^3 and
+    64^3 with the workload's physics, each at one thread and at every host thread, about
+    budget_s / 6 seconds per leg after a one-step calibration. The headline value is the
+    D3Q27 64^3 leg at every thread."""
     import oracle
 
     oracle.build()
-    threads = os.cpu_count() or 1
-    lam = lam_d3q27()
-    # Calibrate on a small box, then size the sample for about budget_s seconds.
-    cal = (16, 16, 16)
-    f = oracle.init_uniform(1, cal, 1.0, U0, AMP, SEED)
-    t = time.perf_counter()
-    oracle.run(1, cal, lam, KBT, SEED, f, 0, 1, threads=threads)
-    per_site = (time.perf_counter() - t) / np.prod(cal)
-    steps = 4
-    dims = _oracle_sample_dims(min(budget_s / (per_site * steps), 64 ** 3))
-    f = oracle.init_uniform(1, dims, 1.0, U0, AMP, SEED)
-    t = time.perf_counter()
-    oracle.run(1, dims, lam, KBT, SEED, f, 0, steps, threads=threads)
-    dt = time.perf_counter() - t
-    value = np.prod(dims) * steps / dt / 1e9
-    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"D3Q27 {dims[0]}x{dims[1]}x{dims[2]} (same physics as the workload), "
-                      f"{steps} steps, {dt:.1f} s, FP64 dense T(u)+LU, OpenMP over sites"}
+    nproc = os.cpu_count() or 1
+    legs = []
+    leg_s = budget_s / (2 * len(CPU_LEGS))
+    per_site = {}  # (lattice, threads) -> seconds per site update of the first (smaller) box
+    for lattice, dims in CPU_LEGS:
+        lam = _lam_for(lattice)
+        u0 = U0 if lattice else U0[:2] + (0.0,)
+        sites = int(np.prod(dims))
+        for threads in (1, nproc):
+            f = oracle.init_uniform(lattice, dims, 1.0, u0, AMP, SEED)
+            if (lattice, threads) not in per_site:  # calibrate with one step
+                t = time.perf_counter()
+                f = oracle.run(lattice, dims, lam, KBT, SEED, f, 0, 1, threads=threads)
+                per_site[(lattice, threads)] = (time.perf_counter() - t) / sites
+            steps = max(1, int(round(leg_s / max(per_site[(lattice, threads)] * sites, 1e-6))))
+            t = time.perf_counter()
+            oracle.run(lattice, dims, lam, KBT, SEED, f, 1, steps, threads=threads)
+            dt = time.perf_counter() - t
+            legs.append({"lattice": "D2Q9" if lattice == 0 else "D3Q27", "dims": list(dims), "threads": threads,
+                         "steps": steps, "seconds": round(dt, 3),
+                         "mlups": round(sites * steps / dt / 1e6, 4)})
+    head = [g for g in legs if g["lattice"] == "D3Q27" and g["dims"] == [64, 64, 64] and g["threads"] == nproc][0]
+    return {"value": head["mlups"] / 1e3, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"D3Q27 64^3 (same physics as the workload), {head['steps']} steps, {head['seconds']} s at "
+                      f"{nproc} threads; also D2Q9 512^2 and D3Q27 32^3, each at 1 and {nproc} threads (legs); "
+                      "FP64 dense T(u)+LU, OpenMP over sites",
+            "legs": legs}
 
 
 def run_reference(args):
@@ -594,7 +643,7 @@ def main(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--stats-every", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-budget", type=float, default=15.0)
+    p.add_argument("--cpu-budget", type=float, default=20.0)
     p.add_argument("--ref-budget", type=float, default=120.0)
     p.add_argument("--dims", type=lambda s: [int(x) for x in s.split(",")], default=list(DIMS),
                    help="box for profiling runs (default 256,256,256: the workload)")

@@ -16,7 +16,8 @@ Pass criterion ("1 % at 3 sigma"): the time- and seed-averaged ratio lies within
 and its 3-sigma statistical error (spread of independent samples) is below 0.5 %.
 
 The C2 ensemble (96 runs: D2Q9 512^2 and D3Q27 64^3, kBT 1e-5..1e-3, shear rate 1.0..1.98,
-seeds 0..3) runs as one batch (flbm_batch_*), sampled with flbm_sample.
+seeds 0..3, 10,000 steps of which the first 1000 are discarded) runs as one batch
+(flbm_batch_*), sampled with flbm_sample every 100 steps.
 """
 import json
 import os
@@ -86,7 +87,7 @@ def c2(fl):
                 for seed in range(4):
                     specs.append(dict(lattice=lat, dims=dims, lam=_lam(lat, om), kBT=kbt, rho0=1.0,
                                       seed=seed, om=om))
-    samples = _run_batch(fl, specs, warm=1000, total=6000, every=100)
+    samples = _run_batch(fl, specs, warm=1000, total=10000, every=100)  # 10,000 steps
     return specs, samples
 
 

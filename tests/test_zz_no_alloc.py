@@ -21,6 +21,12 @@ def _q(lattice):
     return {0: 9, 1: 27, 2: 27, 3: 19}[lattice]
 
 
+def _close(got, ref, atol, what):
+    got, ref = np.asarray(got, dtype=float), np.asarray(ref, dtype=float)
+    bad = np.abs(got - ref) > atol
+    assert not bad.any(), f"{what}: {int(bad.sum())} entries differ, max |diff| {np.abs(got - ref).max():.3e}"
+
+
 def _assert_same_stats(got, ref):
     # Both sides sum the same per-site terms with FP64 atomics whose order varies from run
     # to run, so each entry is compared against the size of the terms summed into it
@@ -33,11 +39,11 @@ def _assert_same_stats(got, ref):
     d = np.abs(np.diag(ref["k_cov"]))
     u2 = np.abs(ref["uu"][:3]).max()
     assert got["mass"] == pytest.approx(ref["mass"], rel=tol)
-    np.testing.assert_allclose(got["mom"], ref["mom"], rtol=0, atol=tol * n * np.sqrt(d[0] * u2) + 1e-300)
-    np.testing.assert_allclose(got["u_mean"], ref["u_mean"], rtol=0, atol=tol * np.sqrt(u2) + 1e-300)
-    np.testing.assert_allclose(got["uu"], ref["uu"], rtol=0, atol=tol * u2 + 1e-300)
-    np.testing.assert_allclose(got["k_mean"], ref["k_mean"], rtol=0, atol=tol * np.sqrt(d) + 1e-300)
-    np.testing.assert_allclose(got["k_cov"], ref["k_cov"], rtol=0, atol=tol * np.sqrt(np.outer(d, d)) + 1e-300)
+    _close(got["mom"], ref["mom"], tol * n * np.sqrt(d[0] * u2), "mom")
+    _close(got["u_mean"], ref["u_mean"], tol * np.sqrt(u2), "u_mean")
+    _close(got["uu"], ref["uu"], tol * u2, "uu")
+    _close(got["k_mean"], ref["k_mean"], tol * np.sqrt(d), "k_mean")
+    _close(got["k_cov"], ref["k_cov"], tol * np.sqrt(np.outer(d, d)), "k_cov")
 
 
 @pytest.mark.parametrize("lattice,dims,storage", [
