@@ -603,7 +603,9 @@ def run_profile_workload(args):
     """A short run of one kernel family for ncu captures (no timing, no bench line):
     stats: a D3Q27 box of --dims, two steps, two statistics reductions; d3q19: a D3Q19 box
     of --dims with the paper's rates (shear 1.6), four steps of --variant (default 2);
-    batch: the 256-lattice ensemble, three steps of the per-step five-blocks form."""
+    batch: the 256-lattice ensemble, three steps of the per-step five-blocks form;
+    step: the headline physics on a D3Q27 box of --dims in --storage, four steps of
+    --variant (default 5)."""
     import torch
 
     import paper_2602_16486_gb300 as fl
@@ -616,6 +618,12 @@ def run_profile_workload(args):
             lat.step(2)
             lat.stats()
             lat.stats()
+    elif args.profile == "step":
+        with fl.Lattice(fl.FLBM_D3Q27, dims, lam_d3q27(), KBT, 1.0, SEED, args.storage) as lat:
+            lat.variant = args.variant or 5
+            lat.init_uniform(U0, AMP, SEED)
+            lat.step(4)
+            lat.sync()
     elif args.profile == "d3q19":
         lam = np.ones(19)
         lam[[7, 8, 9]] = OMEGA
@@ -652,7 +660,9 @@ def main(argv=None):
                    help="step-kernel variant (1-6); default 0 = autotune")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the 16-bit storage, other-lattice and batched-ensemble measurements")
-    p.add_argument("--profile", choices=["stats", "d3q19", "batch"], default=None,
+    p.add_argument("--storage", type=int, default=0, choices=[0, 1, 2],
+                   help="storage of the --profile step workload: 0 FP32, 1 BF16, 2 FP16")
+    p.add_argument("--profile", choices=["stats", "d3q19", "batch", "step"], default=None,
                    help="run a short workload of one kernel family for ncu captures and exit")
     args = p.parse_args(argv)
     if args.profile:

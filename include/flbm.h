@@ -356,6 +356,91 @@ int flbm_batch_sync(flbm_batch *b);
  */
 int flbm_batch_test_wait_timeout(flbm_batch *b, uint32_t polls);
 
+/*
+ * Domain decomposition. One periodic 3-D lattice (FLBM_D3Q27, FLBM_D3Q27_ISO, FLBM_D3Q19)
+ * split along z into slabs of whole planes, for several GPUs (one slab each) or several
+ * slabs on one GPU. The update is the fused step of flbm_step with the periodic streaming
+ * of Eq. streaming across the whole lattice; the noise is keyed on the global site
+ * x + nx (y + ny z), so a decomposed lattice evolves bitwise like the whole one.
+ *
+ * A slab's device array holds its z_count owned planes between two ghost planes, laid out
+ * [q][p][y][x] with p = 0 .. z_count + 1 (p = 1 .. z_count are the global planes z_begin
+ * .. z_begin + z_count - 1). With the in-place AA pattern, a step taken from an even step
+ * count touches only each site's own slots and needs no exchange. A step taken from an
+ * odd step count reads and writes the neighbours' slots, so around it the slots of the
+ * velocities with c_z != 0 move across each slab face (9 slots per face site for D3Q27,
+ * 5 for D3Q19):
+ *   phase 0, before the step: each boundary plane's slots of the velocities leaving through
+ *            the face are copied into the neighbour's ghost plane;
+ *   phase 1, after the step:  the ghost plane's slots the step wrote are copied back to the
+ *            neighbour's boundary plane.
+ * No other slot of a boundary plane is touched by the neighbour, so these are the only
+ * transfers. Statistics and population reads of a slab in an odd state need phase 0 done.
+ */
+
+/* Bytes of a slab's local array (owned and ghost planes); 0 for invalid arguments. */
+size_t flbm_slab_required_bytes(int lattice, const int64_t dims[3], int64_t z_count, int storage);
+
+/*
+ * flbm_create_slab - context of the owned planes [z_begin, z_begin + z_count) of the
+ * lattice dims (global {nx, ny, nz}); other arguments as flbm_create_ex (dev_buf, if
+ * given, >= flbm_slab_required_bytes and 256-byte aligned). The context works as any other
+ * with these differences: flbm_step advances at most one step per call (the caller
+ * exchanges the halo, see flbm_slab_halo, around every step taken from an odd step count);
+ * flbm_stats covers the owned planes only (sites = nx ny z_count; add slabs' sums to
+ * combine); flbm_get/set_populations, flbm_save/load cover the whole local array, ghost
+ * planes included; flbm_autotune is refused (FLBM_ESTATE); step variant 4 runs as 2.
+ * Errors: FLBM_EINVAL for D2Q9, a plane range outside [0, nz) or a local array of 2^32
+ * sites or more.
+ */
+int flbm_create_slab(flbm_ctx **out, int lattice, const int64_t dims[3], int64_t z_begin, int64_t z_count,
+                     const double *lambda, double kBT, double rho0, uint64_t seed, int storage, void *cuda_stream,
+                     void *dev_buf, size_t dev_buf_bytes);
+
+/*
+ * flbm_slab_halo - the regions of one halo message of a slab with z_count owned planes
+ * (host only; needs no GPU). phase: 0 (before the step) or 1 (after it); side: 0 for the
+ * message exchanged with the neighbour below (planes z_begin - 1 ...), 1 with the one above.
+ * On return region k (k < *n_regions, at most 9) of the message is the run of *region_len
+ * = nx * ny elements starting at element send_offset[k] of this slab's array (what this
+ * slab sends), and the matching region of the neighbour's message lands at element
+ * recv_offset[k] of this slab's array. Region k of a (phase, side 0) message pairs with
+ * region k of the lower neighbour's (phase, side 1) message, and vice versa, so a message
+ * is sent and received region by region in this order. Every output array holds 9 entries.
+ */
+int flbm_slab_halo(int lattice, const int64_t dims[3], int64_t z_count, int phase, int side,
+                   int64_t *send_offset, int64_t *recv_offset, int *n_regions, int64_t *region_len);
+
+/*
+ * A domain: nslabs slabs of one lattice in this process, planes split as evenly as
+ * possible (the first nz mod nslabs slabs one plane thicker), slab k on devices[k] (or
+ * every slab on the current device when devices is NULL), each with its own stream; the
+ * halo moves by cudaMemcpyAsync between the slabs' arrays (peer copies across devices),
+ * ordered by events. Every slab starts at rest at step 0.
+ *   flbm_domain_step        : enqueue n steps of the whole lattice (never synchronises).
+ *   flbm_domain_stats       : statistics of the whole lattice, the slabs' FP64 sums added;
+ *                             synchronises; FLBM_ENUMERIC as flbm_stats.
+ *   flbm_domain_get/set_populations : logical FP64 populations of the whole lattice,
+ *                             [q][z][y][x]; synchronise.
+ *   flbm_domain_slab        : borrowed context of slab k (read-only use; NULL if no such
+ *                             slab); flbm_destroy ignores it.
+ *   flbm_domain_set_step_variant : as flbm_set_step_variant, for every slab.
+ */
+typedef struct flbm_domain flbm_domain;
+int flbm_domain_create(flbm_domain **out, int lattice, const int64_t dims[3], const double *lambda, double kBT,
+                       double rho0, uint64_t seed, int storage, int nslabs, const int *devices);
+void flbm_domain_destroy(flbm_domain *d);
+int flbm_domain_size(const flbm_domain *d);
+flbm_ctx *flbm_domain_slab(flbm_domain *d, int k);
+int flbm_domain_init_uniform(flbm_domain *d, const double u0[3], double rho_perturb_amp, uint64_t perturb_seed);
+int flbm_domain_step(flbm_domain *d, int64_t n);
+int64_t flbm_domain_get_step(const flbm_domain *d);
+int flbm_domain_set_step_variant(flbm_domain *d, int variant);
+int flbm_domain_stats(flbm_domain *d, flbm_stats_t *out);
+int flbm_domain_get_populations(flbm_domain *d, double *host, size_t count);
+int flbm_domain_set_populations(flbm_domain *d, const double *host, size_t count);
+int flbm_domain_sync(flbm_domain *d);
+
 #ifdef __cplusplus
 }
 #endif

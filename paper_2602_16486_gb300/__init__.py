@@ -5,4 +5,4 @@ ABI in ``include/flbm.h``); ``flbm`` is its ctypes binding. Importing this packa
 fails loudly when the library has not been built.
 """
 from .flbm import *  # noqa: F401,F403
-from .flbm import Lattice, FlbmError, flbm_stats_t, LIB_PATH  # noqa: F401
+from .flbm import Lattice, Batch, Domain, FlbmError, flbm_stats_t, LIB_PATH  # noqa: F401

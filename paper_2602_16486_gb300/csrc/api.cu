@@ -20,6 +20,7 @@
 
 #include "../../include/flbm.h"
 #include "internal.h"
+#include "lattice.cuh"
 
 using namespace flbm;
 
@@ -53,6 +54,13 @@ struct flbm_ctx {
   StepArgs args{};
   flbm_batch *owner = nullptr;  // set for a lattice of a batch (borrowed handle)
   bool params_changed = false;  // a lattice of a batch reloaded its parameters
+  // One slab of a lattice decomposed along z (flbm_create_slab): dims and N describe the
+  // local array, whose planes 1 .. z_count are the global planes z_begin .. z_begin +
+  // z_count - 1 and whose planes 0 and z_count + 1 are ghost copies of the neighbours'.
+  bool slab = false;
+  int64_t gdims[3] = {1, 1, 1};  // the whole lattice
+  int64_t z_begin = 0, z_count = 0;
+  bool in_domain = false;  // a slab owned by a flbm_domain (stepped by it)
 };
 
 namespace {
@@ -142,6 +150,11 @@ void fill_args(flbm_ctx *c) {
   a.nz = int(c->dims[2]);
   a.rho0 = float(c->rho0);
   a.status = c->d_status;
+  a.z_lo = c->slab ? 1 : 0;
+  a.nz_grid = c->slab ? int(c->z_count) : a.nz;
+  // Global index of local site 0: nx ny (z_begin - 1), taken mod 2^32 (the ghost plane
+  // below z_begin = 0 wraps; it is never updated).
+  a.site_base = c->slab ? uint32_t(uint64_t(int64_t(c->dims[0] * c->dims[1]) * (c->z_begin - 1))) : 0u;
   a.key0 = uint32_t(c->seed);
   a.key1 = uint32_t(c->seed >> 32);
   for (int r = 0; r < 10; ++r) {  // Weyl key schedule of Philox4x32 (Salmon et al., SC'11)
@@ -201,6 +214,12 @@ int ensure_stage(flbm_ctx *c, size_t elems) {
 // column c = [1, rho - rho0, j, u, k_{D+1} .. k_{Q-1}, 0 ...] (NC columns; stats.cu),
 // then the non-finite count. k_0 = rho = rho0 + (rho - rho0) is rebuilt in FP64; the
 // central moments k_1..k_D vanish identically and are reported as 0.
+// Sites the statistics cover: the whole box, or a slab's owned planes.
+long long stat_site0(const flbm_ctx *c) { return c->slab ? (long long)(c->dims[0] * c->dims[1]) : 0; }
+long long stat_sites(const flbm_ctx *c) {
+  return c->slab ? (long long)(c->dims[0] * c->dims[1] * c->z_count) : c->N;
+}
+
 void fill_stats(const flbm_ctx *c, const double *acc, int64_t step, flbm_stats_t *out) {
   const int Q = c->Q, D = c->D;
   const int NC = D == 3 ? 32 : 16;
@@ -210,11 +229,11 @@ void fill_stats(const flbm_ctx *c, const double *acc, int64_t step, flbm_stats_t
   };
   std::memset(out, 0, sizeof(*out));
   out->step = step;
-  out->sites = c->N;
+  out->sites = stat_sites(c);
   out->lattice = c->lattice;
   out->q = Q;
   out->nonfinite = (int64_t)llround(acc[NC * (NC + 1) / 2]);
-  const double inv = 1.0 / double(c->N);
+  const double inv = 1.0 / double(stat_sites(c));
   const double rho0 = c->rho0, cnt = G(0, 0), sd = G(0, 1);
   out->mass = rho0 * cnt + sd;
   for (int a = 0; a < 3; ++a) {
@@ -243,7 +262,8 @@ void fill_stats(const flbm_ctx *c, const double *acc, int64_t step, flbm_stats_t
 int enqueue_stats(flbm_ctx *c, double *acc_dev) {
   FLBM_CUDA(cudaMemsetAsync(acc_dev, 0, sizeof(double) * stats_record_len(c->Q), c->stream));
   FLBM_CUDA(launch_stats(klat(c->lattice), c->storage, c->iso, int(c->step & 1), c->f, c->N, int(c->dims[0]),
-                         int(c->dims[1]), int(c->dims[2]), float(c->rho0), acc_dev, c->stream));
+                         int(c->dims[1]), int(c->dims[2]), float(c->rho0), acc_dev, c->stream, stat_site0(c),
+                         stat_sites(c)));
   return FLBM_OK;
 }
 
@@ -254,7 +274,7 @@ int resolve_variant(const flbm_ctx *c) {
   const bool pipe = pipe_applicable(c->D, c->storage, int(c->dims[0]));
   int v = c->variant;
   if (v == kStepAuto) v = kStepPair;
-  if (v == kStepPipelined && !pipe) v = kStepPair;
+  if (v == kStepPipelined && (!pipe || c->slab)) v = kStepPair;  // the pipelined kernel walks whole boxes
   if (pair_variants_only(c->lattice)) {  // unrolled two-site kernels only
     if (v == kStepPairRolled || v == kStepPipelined) v = kStepPair;
     if (v == kStepPairRolledOcc) v = kStepPairOcc;
@@ -384,7 +404,7 @@ int flbm_create(flbm_ctx **out, int lattice, const int64_t dims[3], const double
 }
 
 void flbm_destroy(flbm_ctx *ctx) {
-  if (!ctx || ctx->owner) return;
+  if (!ctx || ctx->owner || ctx->in_domain) return;
   DeviceGuard g(ctx->device);
   release(ctx);
 }
@@ -400,7 +420,7 @@ int flbm_init_uniform(flbm_ctx *c, const double u0[3], double amp, uint64_t pert
   DeviceGuard g(c->device);
   FLBM_CUDA(launch_init(klat(c->lattice), c->storage, c->f, c->N, int(c->dims[0]), int(c->dims[1]),
                         int(c->dims[2]), c->rho0, u0[0], u0[1], c->D == 3 ? u0[2] : 0.0, amp,
-                        perturb_seed, c->stream));
+                        perturb_seed, c->args.site_base, c->stream));
   c->step = 0;
   return FLBM_OK;
 }
@@ -409,6 +429,9 @@ int flbm_step(flbm_ctx *c, int64_t n) {
   if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
   if (c->owner) return fail(FLBM_ESTATE, "a lattice of a batch advances with flbm_batch_step");
   if (n < 0) return fail(FLBM_EINVAL, "n = %lld must be >= 0", (long long)n);
+  if (c->slab && n > 1)
+    return fail(FLBM_EINVAL, "a slab advances one step per flbm_step call (its halo is exchanged around every "
+                             "step taken from an odd step count, see flbm_slab_halo)");
   DeviceGuard g(c->device);
   const bool noise = c->kBT > 0.0;
   for (int64_t s = 0; s < n; ++s) {
@@ -641,6 +664,7 @@ int flbm_get_step_variant(const flbm_ctx *c) { return c ? resolve_variant(c) : -
 int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
   if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
   if (c->owner) return fail(FLBM_ESTATE, "a lattice of a batch is tuned with flbm_batch_autotune");
+  if (c->slab) return fail(FLBM_ESTATE, "a slab is not tuned alone (its steps need halo exchanges)");
   if (trial_steps < 2) return fail(FLBM_EINVAL, "trial_steps must be >= 2");
   DeviceGuard g(c->device);
   // Cache: one choice per (device, lattice, storage, nx parity, size class, noise).
@@ -1272,7 +1296,7 @@ extern "C" int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storag
   FLBM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * size_t(len), s));
   FLBM_CUDA(launch_stats(klat(lattice), storage, lattice == FLBM_D3Q27_ISO, parity, dev_populations, N,
                          int(dims[0]), int(dims[1]),
-                         int(dims[2]), float(rho0), acc, s));
+                         int(dims[2]), float(rho0), acc, s, 0, N));
   double h[FLBM_NOALLOC_SCRATCH_DOUBLES];
   FLBM_CUDA(cudaMemcpyAsync(h, acc, sizeof(double) * size_t(len), cudaMemcpyDeviceToHost, s));
   FLBM_CUDA(cudaStreamSynchronize(s));
@@ -1288,3 +1312,411 @@ extern "C" int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storag
     return fail(FLBM_ENUMERIC, "%lld sites hold non-finite values", (long long)out->nonfinite);
   return FLBM_OK;
 }
+
+// ---- domain decomposition along z -------------------------------------------------------
+// A lattice split into slabs of whole planes (flbm_create_slab, flbm_domain_*). Each slab
+// keeps its owned planes between two ghost planes. With the in-place AA pattern a step
+// taken from an even step count reads and writes only the site's own slots, so it needs
+// no exchange; a step taken from an odd count reads slot opposite(i) of x - c_i and
+// writes slot i of x + c_i, which crosses the slab faces for the velocities with c_z != 0.
+// Around such a step the slots of those velocities move between the owned boundary planes
+// and the neighbours' ghost planes: before it (phase 0) each boundary plane's slots of the
+// velocities leaving through the face are copied into the neighbour's ghost plane; after
+// it (phase 1) the ghost plane's slots written by the step go back to their owner. No
+// other slot of a boundary plane is read or written by the neighbour, so the copies need
+// no further ordering with the neighbour's own step. The noise is keyed on the global
+// site, so a decomposed lattice steps bitwise like the whole one.
+namespace {
+
+int check_slab(int lattice, const int64_t dims[3], int64_t z_begin, int64_t z_count, int storage) {
+  int st = check_geometry(lattice, dims, storage);
+  if (st != FLBM_OK) return st;
+  if (lattice == FLBM_D2Q9)
+    return fail(FLBM_EINVAL, "slabs split a 3-D lattice along z; D2Q9 is not decomposed");
+  if (z_begin < 0 || z_begin >= dims[2])
+    return fail(FLBM_EINVAL, "z_begin = %lld outside [0, %lld)", (long long)z_begin, (long long)dims[2]);
+  if (z_count < 1 || z_begin + z_count > dims[2])
+    return fail(FLBM_EINVAL, "z_count = %lld must lie in [1, nz - z_begin]", (long long)z_count);
+  if (z_count + 2 > 65535) return fail(FLBM_EINVAL, "a slab holds at most 65533 planes");
+  if (double(dims[0]) * double(dims[1]) * double(z_count + 2) >= 4294967296.0)
+    return fail(FLBM_EINVAL, "a slab's local array (owned and ghost planes) must hold < 2^32 sites");
+  return FLBM_OK;
+}
+
+// Slots of the velocities with c_z = +1 (dir > 0) or -1 (dir < 0), in index order.
+int z_slots(int lattice, int dir, int *out) {
+  const int Q = q_of(lattice);
+  int n = 0;
+  for (int i = 0; i < Q; ++i) {
+    const int cz = Lat<3>::cz(i);  // D3Q19 takes the first 19 D3Q27 velocities
+    if ((dir > 0 && cz == 1) || (dir < 0 && cz == -1)) out[n++] = i;
+  }
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t flbm_slab_required_bytes(int lattice, const int64_t dims[3], int64_t z_count, int storage) {
+  const std::string saved = g_last_error;
+  if (!dims || check_slab(lattice, dims, 0, z_count, storage) != FLBM_OK) return 0;
+  g_last_error = saved;
+  return size_t(q_of(lattice)) * size_t(dims[0] * dims[1] * (z_count + 2)) * storage_bytes(storage);
+}
+
+int flbm_slab_halo(int lattice, const int64_t dims[3], int64_t z_count, int phase, int side,
+                   int64_t *send_offset, int64_t *recv_offset, int *n_regions, int64_t *region_len) {
+  int st = check_slab(lattice, dims, 0, z_count, FLBM_FP32);
+  if (st != FLBM_OK) return st;
+  if (phase != 0 && phase != 1) return fail(FLBM_EINVAL, "phase must be 0 or 1, got %d", phase);
+  if (side != 0 && side != 1) return fail(FLBM_EINVAL, "side must be 0 (lower) or 1 (upper), got %d", side);
+  if (!send_offset || !recv_offset || !n_regions || !region_len) return fail(FLBM_EINVAL, "NULL output");
+  const int64_t pl = dims[0] * dims[1];          // sites per plane
+  const int64_t N = pl * (z_count + 2);          // sites of the local array
+  const int64_t top = z_count, ghost_hi = z_count + 1;
+  // (plane sent, slot set sent, plane received, slot set received); slot sets by c_z sign.
+  int64_t p_send, p_recv;
+  int d_send, d_recv;
+  if (phase == 0) {  // owned boundary plane -> neighbour's ghost plane
+    if (side == 0) { p_send = 1; d_send = +1; p_recv = 0; d_recv = -1; }
+    else           { p_send = top; d_send = -1; p_recv = ghost_hi; d_recv = +1; }
+  } else {           // ghost plane -> its owner's boundary plane
+    if (side == 0) { p_send = 0; d_send = -1; p_recv = 1; d_recv = +1; }
+    else           { p_send = ghost_hi; d_send = +1; p_recv = top; d_recv = -1; }
+  }
+  int ss[27], rs[27];
+  const int ns = z_slots(lattice, d_send, ss), nr = z_slots(lattice, d_recv, rs);
+  if (ns != nr) return fail(FLBM_EINVAL, "internal: slot sets differ in size");
+  for (int k = 0; k < ns; ++k) {
+    send_offset[k] = int64_t(ss[k]) * N + p_send * pl;
+    recv_offset[k] = int64_t(rs[k]) * N + p_recv * pl;
+  }
+  *n_regions = ns;
+  *region_len = pl;
+  return FLBM_OK;
+}
+
+int flbm_create_slab(flbm_ctx **out, int lattice, const int64_t dims[3], int64_t z_begin, int64_t z_count,
+                     const double *lambda, double kBT, double rho0, uint64_t seed, int storage, void *cuda_stream,
+                     void *dev_buf, size_t dev_buf_bytes) {
+  if (!out) return fail(FLBM_EINVAL, "out is NULL");
+  if (!dims) return fail(FLBM_EINVAL, "dims is NULL");
+  int st = check_slab(lattice, dims, z_begin, z_count, storage);
+  if (st != FLBM_OK) return st;
+  const int64_t local[3] = {dims[0], dims[1], z_count + 2};
+  flbm_ctx *c = nullptr;
+  st = flbm_create_ex(&c, lattice, local, lambda, kBT, rho0, seed, storage, cuda_stream, dev_buf, dev_buf_bytes);
+  if (st != FLBM_OK) return st;
+  c->slab = true;
+  for (int a = 0; a < 3; ++a) c->gdims[a] = dims[a];
+  c->z_begin = z_begin;
+  c->z_count = z_count;
+  fill_args(c);
+  *out = c;
+  return FLBM_OK;
+}
+
+}  // extern "C"
+
+struct flbm_domain {
+  int lattice = 1, Q = 27, storage = 0;
+  int64_t dims[3] = {1, 1, 1};
+  double rho0 = 1.0;
+  std::vector<flbm_ctx *> slabs;
+  std::vector<cudaEvent_t> done;  // per slab: its last work that neighbours wait for
+  int64_t step = 0;
+  bool ghosts_filled = false;  // phase-0 copies made for the current (odd) state
+};
+
+namespace {
+
+void domain_release(flbm_domain *d) {
+  if (!d) return;
+  for (size_t k = 0; k < d->slabs.size(); ++k) {
+    flbm_ctx *c = d->slabs[k];
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (k < d->done.size() && d->done[k]) cudaEventDestroy(d->done[k]);
+    c->in_domain = false;
+    release(c);
+  }
+  delete d;
+}
+
+int domain_record(flbm_domain *d) {
+  for (size_t k = 0; k < d->slabs.size(); ++k) {
+    DeviceGuard g(d->slabs[k]->device);
+    FLBM_CUDA(cudaEventRecord(d->done[k], d->slabs[k]->stream));
+  }
+  return FLBM_OK;
+}
+
+// Slab k's stream waits for the last recorded work of its two neighbours (periodic in z).
+int domain_wait_neighbours(flbm_domain *d, size_t k) {
+  const size_t n = d->slabs.size(), lo = (k + n - 1) % n, hi = (k + 1) % n;
+  DeviceGuard g(d->slabs[k]->device);
+  FLBM_CUDA(cudaStreamWaitEvent(d->slabs[k]->stream, d->done[lo], 0));
+  if (hi != lo) FLBM_CUDA(cudaStreamWaitEvent(d->slabs[k]->stream, d->done[hi], 0));
+  return FLBM_OK;
+}
+
+// Copies of one message: `from`'s send regions of (phase, side) into `to`'s receive
+// regions of (phase, 1 - side), on `stream`.
+int domain_copy(const flbm_domain *d, const flbm_ctx *from, const flbm_ctx *to, int phase, int side,
+                cudaStream_t stream) {
+  int64_t so[27], ro_unused[27], so_unused[27], ro[27], len = 0, len2 = 0;
+  int n = 0, n2 = 0;
+  int st = flbm_slab_halo(d->lattice, d->dims, from->z_count, phase, side, so, ro_unused, &n, &len);
+  if (st == FLBM_OK) st = flbm_slab_halo(d->lattice, d->dims, to->z_count, phase, 1 - side, so_unused, ro, &n2, &len2);
+  if (st != FLBM_OK) return st;
+  const size_t es = storage_bytes(d->storage);
+  for (int k = 0; k < n; ++k) {
+    const char *src = static_cast<const char *>(from->f) + size_t(so[k]) * es;
+    char *dst = static_cast<char *>(to->f) + size_t(ro[k]) * es;
+    FLBM_CUDA(cudaMemcpyAsync(dst, src, size_t(len) * es, cudaMemcpyDefault, stream));
+  }
+  return FLBM_OK;
+}
+
+// Phase 0: every slab fills its ghost planes from its neighbours' boundary planes.
+int domain_fill_ghosts(flbm_domain *d) {
+  int st = domain_record(d);
+  const size_t n = d->slabs.size();
+  for (size_t k = 0; k < n && st == FLBM_OK; ++k) {
+    st = domain_wait_neighbours(d, k);
+    flbm_ctx *me = d->slabs[k], *lo = d->slabs[(k + n - 1) % n], *hi = d->slabs[(k + 1) % n];
+    DeviceGuard g(me->device);
+    if (st == FLBM_OK) st = domain_copy(d, lo, me, 0, 1, me->stream);  // lower's top -> my lower ghost
+    if (st == FLBM_OK) st = domain_copy(d, hi, me, 0, 0, me->stream);  // upper's bottom -> my upper ghost
+  }
+  if (st == FLBM_OK) st = domain_record(d);
+  if (st == FLBM_OK) d->ghosts_filled = true;
+  return st;
+}
+
+// Phase 1: every slab returns the ghost slots its step wrote to their owners.
+int domain_return_ghosts(flbm_domain *d) {
+  const size_t n = d->slabs.size();
+  int st = FLBM_OK;
+  for (size_t k = 0; k < n && st == FLBM_OK; ++k) {
+    flbm_ctx *me = d->slabs[k], *lo = d->slabs[(k + n - 1) % n], *hi = d->slabs[(k + 1) % n];
+    DeviceGuard g(me->device);
+    st = domain_copy(d, me, lo, 1, 0, me->stream);        // my lower ghost -> lower's top plane
+    if (st == FLBM_OK) st = domain_copy(d, me, hi, 1, 1, me->stream);  // my upper ghost -> upper's bottom
+  }
+  if (st == FLBM_OK) st = domain_record(d);
+  return st;
+}
+
+int domain_view(const flbm_domain *d, flbm_ctx *view) {
+  view->lattice = d->lattice;
+  view->D = 3;
+  view->Q = d->Q;
+  view->N = (long long)(d->dims[0] * d->dims[1] * d->dims[2]);
+  view->rho0 = d->rho0;
+  return FLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int flbm_domain_create(flbm_domain **out, int lattice, const int64_t dims[3], const double *lambda, double kBT,
+                       double rho0, uint64_t seed, int storage, int nslabs, const int *devices) {
+  if (!out) return fail(FLBM_EINVAL, "out is NULL");
+  if (!dims) return fail(FLBM_EINVAL, "dims is NULL");
+  if (nslabs < 1 || nslabs > dims[2])
+    return fail(FLBM_EINVAL, "nslabs = %d must lie in [1, nz = %lld]", nslabs, (long long)dims[2]);
+  int st = check_slab(lattice, dims, 0, (dims[2] + nslabs - 1) / nslabs, storage);
+  if (st != FLBM_OK) return st;
+  st = check_params(lattice, lambda, kBT, rho0);
+  if (st != FLBM_OK) return st;
+  int cur = 0;
+  FLBM_CUDA(cudaGetDevice(&cur));
+  flbm_domain *d = new (std::nothrow) flbm_domain();
+  if (!d) return fail(FLBM_ENOMEM, "host allocation failed");
+  d->lattice = lattice;
+  d->Q = q_of(lattice);
+  d->storage = storage;
+  d->rho0 = rho0;
+  for (int a = 0; a < 3; ++a) d->dims[a] = dims[a];
+  // Planes split as evenly as possible, the first nz mod nslabs slabs one plane thicker.
+  int64_t z = 0;
+  for (int k = 0; k < nslabs; ++k) {
+    const int64_t zc = dims[2] / nslabs + (k < dims[2] % nslabs ? 1 : 0);
+    const int dev = devices ? devices[k] : cur;
+    flbm_ctx *c = nullptr;
+    {
+      DeviceGuard g(dev);
+      if (!g.ok) {
+        domain_release(d);
+        return fail(FLBM_EINVAL, "cannot make device %d current", dev);
+      }
+      st = flbm_create_slab(&c, lattice, dims, z, zc, lambda, kBT, rho0, seed, storage, nullptr, nullptr, 0);
+      cudaEvent_t e = nullptr;
+      if (st == FLBM_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        release(c);
+        st = fail(FLBM_ECUDA, "cudaEventCreate failed");
+      }
+      if (st != FLBM_OK) {
+        const std::string msg = g_last_error;
+        domain_release(d);
+        return fail(st, "slab %d: %s", k, msg.c_str());
+      }
+      c->in_domain = true;
+      d->slabs.push_back(c);
+      d->done.push_back(e);
+    }
+    z += zc;
+  }
+  const int rs = domain_record(d);
+  if (rs != FLBM_OK) {
+    domain_release(d);
+    return rs;
+  }
+  *out = d;
+  return FLBM_OK;
+}
+
+void flbm_domain_destroy(flbm_domain *d) { domain_release(d); }
+
+int flbm_domain_size(const flbm_domain *d) { return d ? int(d->slabs.size()) : -1; }
+
+flbm_ctx *flbm_domain_slab(flbm_domain *d, int k) {
+  if (!d || k < 0 || k >= int(d->slabs.size())) {
+    fail(FLBM_EINVAL, "no slab %d in this domain", k);
+    return nullptr;
+  }
+  return d->slabs[size_t(k)];
+}
+
+int flbm_domain_init_uniform(flbm_domain *d, const double u0[3], double amp, uint64_t perturb_seed) {
+  if (!d) return fail(FLBM_EINVAL, "domain is NULL");
+  for (flbm_ctx *c : d->slabs) {
+    const int st = flbm_init_uniform(c, u0, amp, perturb_seed);
+    if (st != FLBM_OK) return st;
+  }
+  d->step = 0;
+  d->ghosts_filled = false;
+  return domain_record(d);
+}
+
+int flbm_domain_step(flbm_domain *d, int64_t n) {
+  if (!d) return fail(FLBM_EINVAL, "domain is NULL");
+  if (n < 0) return fail(FLBM_EINVAL, "n = %lld must be >= 0", (long long)n);
+  for (int64_t s = 0; s < n; ++s) {
+    const bool odd = (d->step & 1) != 0;
+    int st = FLBM_OK;
+    if (odd && !d->ghosts_filled) st = domain_fill_ghosts(d);
+    for (size_t k = 0; k < d->slabs.size() && st == FLBM_OK; ++k) {
+      st = domain_wait_neighbours(d, k);
+      if (st == FLBM_OK) st = flbm_step(d->slabs[k], 1);
+    }
+    if (st == FLBM_OK) st = odd ? domain_return_ghosts(d) : domain_record(d);
+    if (st != FLBM_OK) return st;
+    d->ghosts_filled = false;
+    ++d->step;
+  }
+  return FLBM_OK;
+}
+
+int64_t flbm_domain_get_step(const flbm_domain *d) { return d ? d->step : -1; }
+
+int flbm_domain_set_step_variant(flbm_domain *d, int variant) {
+  if (!d) return fail(FLBM_EINVAL, "domain is NULL");
+  for (flbm_ctx *c : d->slabs) {
+    const int st = flbm_set_step_variant(c, variant);
+    if (st != FLBM_OK) return st;
+  }
+  return FLBM_OK;
+}
+
+int flbm_domain_sync(flbm_domain *d) {
+  if (!d) return fail(FLBM_EINVAL, "domain is NULL");
+  for (flbm_ctx *c : d->slabs) {
+    const int st = flbm_sync(c);
+    if (st != FLBM_OK) return st;
+  }
+  return FLBM_OK;
+}
+
+int flbm_domain_stats(flbm_domain *d, flbm_stats_t *out) {
+  if (!d) return fail(FLBM_EINVAL, "domain is NULL");
+  if (!out) return fail(FLBM_EINVAL, "out is NULL");
+  // An odd state's owned sites read their arriving populations from the ghost planes.
+  if ((d->step & 1) && !d->ghosts_filled) {
+    const int st = domain_fill_ghosts(d);
+    if (st != FLBM_OK) return st;
+  }
+  const size_t len = size_t(stats_record_len(d->Q));
+  std::vector<double> sum(len, 0.0);
+  for (size_t k = 0; k < d->slabs.size(); ++k) {
+    flbm_ctx *c = d->slabs[k];
+    DeviceGuard g(c->device);
+    int st = domain_wait_neighbours(d, k);
+    if (st == FLBM_OK) st = enqueue_stats(c, c->d_acc);
+    if (st != FLBM_OK) return st;
+    FLBM_CUDA(cudaMemcpyAsync(c->h_acc, c->d_acc, sizeof(double) * len, cudaMemcpyDeviceToHost, c->stream));
+    FLBM_CUDA(cudaStreamSynchronize(c->stream));
+    // Every entry of the record is a plain sum over sites (Gram entries and the
+    // non-finite count): the slabs' records add in FP64.
+    for (size_t i = 0; i < len; ++i) sum[i] += c->h_acc[i];
+  }
+  flbm_ctx view;
+  domain_view(d, &view);
+  fill_stats(&view, sum.data(), d->step, out);
+  if (out->nonfinite > 0)
+    return fail(FLBM_ENUMERIC, "%lld sites hold non-finite values at step %lld", (long long)out->nonfinite,
+                (long long)d->step);
+  return FLBM_OK;
+}
+
+int flbm_domain_get_populations(flbm_domain *d, double *host, size_t count) {
+  if (!d) return fail(FLBM_EINVAL, "domain is NULL");
+  if (!host) return fail(FLBM_EINVAL, "host is NULL");
+  const size_t pl = size_t(d->dims[0] * d->dims[1]), N = pl * size_t(d->dims[2]);
+  if (count != size_t(d->Q) * N) return fail(FLBM_EINVAL, "count = %zu, expected Q * sites = %zu", count, size_t(d->Q) * N);
+  if ((d->step & 1) && !d->ghosts_filled) {
+    const int st = domain_fill_ghosts(d);
+    if (st != FLBM_OK) return st;
+  }
+  for (size_t k = 0; k < d->slabs.size(); ++k) {
+    flbm_ctx *c = d->slabs[k];
+    const size_t nl = size_t(c->N);
+    std::vector<double> loc(size_t(d->Q) * nl);
+    int st = domain_wait_neighbours(d, k);
+    if (st == FLBM_OK) st = flbm_get_populations(c, loc.data(), loc.size());
+    if (st != FLBM_OK) return st;
+    for (int q = 0; q < d->Q; ++q)
+      std::memcpy(host + size_t(q) * N + size_t(c->z_begin) * pl, loc.data() + size_t(q) * nl + pl,
+                  sizeof(double) * pl * size_t(c->z_count));
+  }
+  return FLBM_OK;
+}
+
+int flbm_domain_set_populations(flbm_domain *d, const double *host, size_t count) {
+  if (!d) return fail(FLBM_EINVAL, "domain is NULL");
+  if (!host) return fail(FLBM_EINVAL, "host is NULL");
+  const size_t pl = size_t(d->dims[0] * d->dims[1]), N = pl * size_t(d->dims[2]);
+  if (count != size_t(d->Q) * N) return fail(FLBM_EINVAL, "count = %zu, expected Q * sites = %zu", count, size_t(d->Q) * N);
+  // Each slab takes its owned planes and, in its ghost planes, the neighbouring planes of
+  // the whole lattice (periodic): every slot the scatter writes then holds its true value,
+  // whichever slab owns it in the current AA state.
+  for (flbm_ctx *c : d->slabs) {
+    const size_t nl = size_t(c->N);
+    std::vector<double> loc(size_t(d->Q) * nl);
+    for (int64_t p = 0; p < c->z_count + 2; ++p) {
+      const int64_t zg = ((c->z_begin + p - 1) % d->dims[2] + d->dims[2]) % d->dims[2];
+      for (int q = 0; q < d->Q; ++q)
+        std::memcpy(loc.data() + size_t(q) * nl + size_t(p) * pl, host + size_t(q) * N + size_t(zg) * pl,
+                    sizeof(double) * pl);
+    }
+    const int st = flbm_set_populations(c, loc.data(), loc.size());
+    if (st != FLBM_OK) return st;
+  }
+  d->ghosts_filled = false;
+  return domain_record(d);
+}
+
+}  // extern "C"

@@ -22,6 +22,11 @@ struct StepArgs {
   uint32_t key0, key1;        // noise key (seed)
   uint32_t ks0[10], ks1[10];  // Philox round keys: key0 + r 0x9E3779B9, key1 + r 0xBB67AE85
   uint32_t step_lo, step_hi;  // step number of this update
+  // Planes updated: z_lo .. z_lo + nz_grid - 1 (the whole box: 0 and nz; a slab of a
+  // decomposed lattice: its owned planes between two ghost planes), and the global index of
+  // local site 0 (0 for a whole box), added to the local site index that keys the noise.
+  int z_lo, nz_grid;
+  uint32_t site_base;
   int *status;        // device word: nonzero after a bounded wait gave up (pipelined kernel)
   float om[27];       // 1 - Lambda_v (conserved modes: unused)
   float phc[27];      // sqrt(kBT Lambda_v (2 - Lambda_v) b_v / cs^2); phi_v = sqrt(rho) phc_v
@@ -106,11 +111,14 @@ cudaError_t launch_step_d3q19(int storage, int variant, int parity, bool noise, 
                               cudaStream_t s);
 cudaError_t launch_step_pipelined(int D, int storage, int parity, bool noise, bool shear,
                                   const StepArgs &a, cudaStream_t s);
+// Statistics of the sites [site0, site0 + nsites) of the array (the whole box: 0, plane).
 cudaError_t launch_stats(int D, int storage, bool iso, int parity, const void *f, long long plane, int nx,
-                         int ny, int nz, float rho0, double *acc, cudaStream_t s);
+                         int ny, int nz, float rho0, double *acc, cudaStream_t s, long long site0,
+                         long long nsites);
+// site_base: global index of local site 0 (keys the density perturbation).
 cudaError_t launch_init(int D, int storage, void *f, long long plane, int nx, int ny, int nz,
                         double rho0, double ux, double uy, double uz, double amp,
-                        uint64_t perturb_seed, cudaStream_t s);
+                        uint64_t perturb_seed, uint32_t site_base, cudaStream_t s);
 cudaError_t launch_gather_plane(int D, int storage, int parity, const void *f, long long plane,
                                 int nx, int ny, int nz, double rho0, int q, double *out,
                                 cudaStream_t s);

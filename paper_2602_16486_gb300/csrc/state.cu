@@ -37,13 +37,13 @@ __device__ __forceinline__ long long logical_slot(int i, int x, int y, int z, in
 template <int D, typename S>
 __global__ void init_kernel(S *__restrict__ f, long long plane, int nx, int ny, int nz, double rho0,
                             double ux, double uy, double uz, double amp, uint32_t key0,
-                            uint32_t key1) {
+                            uint32_t key1, uint32_t site_base) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= plane) return;
   double rho = rho0;
   if (amp != 0.0) {
     // Tag-1 stream: counter (site, 0, 0, 1 << 16), word 0 -> U in (0, 1).
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)s, 0u, 0u, 1u << 16), key0, key1);
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)s + site_base, 0u, 0u, 1u << 16), key0, key1);
     const double U = (double)uniform01(w.x);
     rho = rho0 * (1.0 + amp * (2.0 * U - 1.0));
   }
@@ -114,15 +114,19 @@ inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) /
 
 template <typename S>
 cudaError_t init_typed(int D, void *f, long long plane, int nx, int ny, int nz, double rho0,
-                       double ux, double uy, double uz, double amp, uint64_t seed, cudaStream_t s) {
+                       double ux, double uy, double uz, double amp, uint64_t seed, uint32_t site_base,
+                       cudaStream_t s) {
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   S *p = static_cast<S *>(f);
   if (D == 19)
-    init_kernel<19, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, ux, uy, uz, amp, k0, k1);
+    init_kernel<19, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, ux, uy, uz, amp, k0, k1,
+                                                              site_base);
   else if (D == 3)
-    init_kernel<3, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, ux, uy, uz, amp, k0, k1);
+    init_kernel<3, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, ux, uy, uz, amp, k0, k1,
+                                                             site_base);
   else
-    init_kernel<2, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, ux, uy, 0.0, amp, k0, k1);
+    init_kernel<2, S><<<blocks_for(plane, 256), 256, 0, s>>>(p, plane, nx, ny, nz, rho0, ux, uy, 0.0, amp, k0, k1,
+                                                             site_base);
   return cudaGetLastError();
 }
 
@@ -173,11 +177,12 @@ size_t storage_bytes(int storage) { return storage == 0 ? 4 : 2; }
 
 cudaError_t launch_init(int D, int storage, void *f, long long plane, int nx, int ny, int nz,
                         double rho0, double ux, double uy, double uz, double amp,
-                        uint64_t perturb_seed, cudaStream_t s) {
-  if (storage == 0) return init_typed<float>(D, f, plane, nx, ny, nz, rho0, ux, uy, uz, amp, perturb_seed, s);
+                        uint64_t perturb_seed, uint32_t site_base, cudaStream_t s) {
+  if (storage == 0)
+    return init_typed<float>(D, f, plane, nx, ny, nz, rho0, ux, uy, uz, amp, perturb_seed, site_base, s);
   if (storage == 1)
-    return init_typed<__nv_bfloat16>(D, f, plane, nx, ny, nz, rho0, ux, uy, uz, amp, perturb_seed, s);
-  return init_typed<__half>(D, f, plane, nx, ny, nz, rho0, ux, uy, uz, amp, perturb_seed, s);
+    return init_typed<__nv_bfloat16>(D, f, plane, nx, ny, nz, rho0, ux, uy, uz, amp, perturb_seed, site_base, s);
+  return init_typed<__half>(D, f, plane, nx, ny, nz, rho0, ux, uy, uz, amp, perturb_seed, site_base, s);
 }
 
 cudaError_t launch_gather_plane(int D, int storage, int parity, const void *f, long long plane,

@@ -132,7 +132,8 @@ __device__ __forceinline__ void pair_columns(const S *__restrict__ f, long long 
 template <int D, typename S, int PARITY, bool PAIRROW, bool ISO>
 __global__ void __launch_bounds__(kStatsBlock, PAIRROW ? 4 : 3) stats_kernel(const S *__restrict__ f, long long plane,
                                                                int nx, int ny, int nz, float rho0,
-                                                               double *__restrict__ acc) {
+                                                               double *__restrict__ acc, long long site0,
+                                                               long long site1) {
   constexpr int NC = StatsPlan<D>::NC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const gram::Smem<D> sm = gram::smem_layout<D>(smem_raw);
@@ -144,9 +145,10 @@ __global__ void __launch_bounds__(kStatsBlock, PAIRROW ? 4 : 3) stats_kernel(con
   gw.init();
 
   unsigned nonfinite = 0u;
-  const long long N = plane;
+  const long long N = site1;  // sites [site0, site1) of the array (plane = its Q-stride)
   int tiles_done = 0;
-  for (long long base = (long long)blockIdx.x * kTileSites; base < N; base += (long long)gridDim.x * kTileSites) {
+  for (long long base = site0 + (long long)blockIdx.x * kTileSites; base < N;
+       base += (long long)gridDim.x * kTileSites) {
     {
       float2 col[NC];
       if constexpr (D == 19) {
@@ -215,55 +217,58 @@ cudaError_t stats_grid(K kernel, size_t smem, long long tiles, int *grid) {
 
 template <int D, typename S, int PARITY, bool PAIRROW, bool ISO>
 cudaError_t launch_one(const S *p, long long plane, int nx, int ny, int nz, float rho0, double *acc,
-                       cudaStream_t s) {
+                       cudaStream_t s, long long site0, long long nsites) {
   auto kernel = stats_kernel<D, S, PARITY, PAIRROW, ISO>;
   const size_t smem = stats_smem<D, S>();
-  const long long tiles = (plane + kTileSites - 1) / kTileSites;
+  const long long tiles = (nsites + kTileSites - 1) / kTileSites;
+  if (tiles == 0) return cudaSuccess;
   int grid = 0;
   const cudaError_t e = stats_grid(kernel, smem, tiles, &grid);
   if (e != cudaSuccess) return e;
-  kernel<<<grid, kStatsBlock, smem, s>>>(p, plane, nx, ny, nz, rho0, acc);
+  kernel<<<grid, kStatsBlock, smem, s>>>(p, plane, nx, ny, nz, rho0, acc, site0, site0 + nsites);
   return cudaGetLastError();
 }
 
 template <int D, typename S, bool ISO>
 cudaError_t launch_typed(int parity, const void *f, long long plane, int nx, int ny, int nz,
-                         float rho0, double *acc, cudaStream_t s) {
+                         float rho0, double *acc, cudaStream_t s, long long site0, long long nsites) {
   const S *p = static_cast<const S *>(f);
-  const bool pairrow = nx % 2 == 0;
+  // Pairs (s, s + 1) share a row when nx is even and every tile starts on an even site.
+  const bool pairrow = nx % 2 == 0 && site0 % 2 == 0;
   if (parity == 0)
-    return pairrow ? launch_one<D, S, 0, true, ISO>(p, plane, nx, ny, nz, rho0, acc, s)
-                   : launch_one<D, S, 0, false, ISO>(p, plane, nx, ny, nz, rho0, acc, s);
-  return pairrow ? launch_one<D, S, 1, true, ISO>(p, plane, nx, ny, nz, rho0, acc, s)
-                 : launch_one<D, S, 1, false, ISO>(p, plane, nx, ny, nz, rho0, acc, s);
+    return pairrow ? launch_one<D, S, 0, true, ISO>(p, plane, nx, ny, nz, rho0, acc, s, site0, nsites)
+                   : launch_one<D, S, 0, false, ISO>(p, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
+  return pairrow ? launch_one<D, S, 1, true, ISO>(p, plane, nx, ny, nz, rho0, acc, s, site0, nsites)
+                 : launch_one<D, S, 1, false, ISO>(p, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
 }
 
 }  // namespace
 
 cudaError_t launch_stats(int D, int storage, bool iso, int parity, const void *f, long long plane, int nx,
-                         int ny, int nz, float rho0, double *acc, cudaStream_t s) {
+                         int ny, int nz, float rho0, double *acc, cudaStream_t s, long long site0,
+                         long long nsites) {
   if (D == 19) {  // D3Q19 (lattice code 19)
-    if (storage == 0) return launch_typed<19, float, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+    if (storage == 0) return launch_typed<19, float, false>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
     if (storage == 1)
-      return launch_typed<19, __nv_bfloat16, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
-    return launch_typed<19, __half, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+      return launch_typed<19, __nv_bfloat16, false>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
+    return launch_typed<19, __half, false>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
   }
   if (D == 3 && iso) {
-    if (storage == 0) return launch_typed<3, float, true>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+    if (storage == 0) return launch_typed<3, float, true>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
     if (storage == 1)
-      return launch_typed<3, __nv_bfloat16, true>(parity, f, plane, nx, ny, nz, rho0, acc, s);
-    return launch_typed<3, __half, true>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+      return launch_typed<3, __nv_bfloat16, true>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
+    return launch_typed<3, __half, true>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
   }
   if (D == 3) {
-    if (storage == 0) return launch_typed<3, float, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+    if (storage == 0) return launch_typed<3, float, false>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
     if (storage == 1)
-      return launch_typed<3, __nv_bfloat16, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
-    return launch_typed<3, __half, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+      return launch_typed<3, __nv_bfloat16, false>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
+    return launch_typed<3, __half, false>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
   }
-  if (storage == 0) return launch_typed<2, float, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+  if (storage == 0) return launch_typed<2, float, false>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
   if (storage == 1)
-    return launch_typed<2, __nv_bfloat16, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
-  return launch_typed<2, __half, false>(parity, f, plane, nx, ny, nz, rho0, acc, s);
+    return launch_typed<2, __nv_bfloat16, false>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
+  return launch_typed<2, __half, false>(parity, f, plane, nx, ny, nz, rho0, acc, s, site0, nsites);
 }
 
 }  // namespace flbm

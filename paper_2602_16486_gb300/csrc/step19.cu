@@ -14,12 +14,12 @@ template <typename S, int PARITY, bool NOISE, bool SHEAR>
 __global__ void __launch_bounds__(kStepBlock) step19_kernel(const StepArgs a) {
   const int x = blockIdx.x * kStepBlock + threadIdx.x;
   if (x >= a.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = blockIdx.y, z = blockIdx.z + a.z_lo;
   const Neighbourhood nb = neighbourhood(x, y, z, a.nx, a.ny, a.nz);
   S *__restrict__ f = static_cast<S *>(a.f);
   float F[19];
   load19<S, PARITY>(f, a.plane, nb, F);
-  const uint32_t site = (uint32_t)(x + (long long)a.nx * (y + (long long)a.ny * z));
+  const uint32_t site = (uint32_t)(x + (long long)a.nx * (y + (long long)a.ny * z)) + a.site_base;
   collide19<NOISE, float, SHEAR>(F, a.rho0, a.om, a.phc, site, a.step_lo, a.step_hi, KeyTable{a.ks0, a.ks1});
   store19<S, PARITY>(f, a.plane, nb, F);
 }
@@ -28,11 +28,11 @@ template <typename S, int PARITY, bool NOISE, bool SHEAR, int MINB>
 __global__ void __launch_bounds__(kStepBlock, MINB) step19_2_kernel(const StepArgs a) {
   const int x0 = 2 * (blockIdx.x * kStepBlock + threadIdx.x);
   if (x0 >= a.nx) return;
-  const Addr2 ad = addr2(x0, blockIdx.y, blockIdx.z, a.nx, a.ny, a.nz);
+  const Addr2 ad = addr2(x0, blockIdx.y, blockIdx.z + a.z_lo, a.nx, a.ny, a.nz);
   S *__restrict__ f = static_cast<S *>(a.f);
   float2 F[19];
   load19_2<S, PARITY>(f, a.plane, ad, F);
-  collide19<NOISE, float2, SHEAR>(F, a.rho0, a.om, a.phc, (uint32_t)ad.s0, a.step_lo, a.step_hi,
+  collide19<NOISE, float2, SHEAR>(F, a.rho0, a.om, a.phc, (uint32_t)ad.s0 + a.site_base, a.step_lo, a.step_hi,
                                   KeyTable{a.ks0, a.ks1});
   store19_2<S, PARITY>(f, a.plane, ad, F);
 }
@@ -41,9 +41,9 @@ template <typename S, int PARITY, bool NOISE, bool SHEAR>
 cudaError_t launch19(int variant, const StepArgs &a, cudaStream_t s) {
   const dim3 block(kStepBlock);
   if (variant == kStepOneSite) {
-    step19_kernel<S, PARITY, NOISE, SHEAR><<<dim3((a.nx + kStepBlock - 1) / kStepBlock, a.ny, a.nz), block, 0, s>>>(a);
+    step19_kernel<S, PARITY, NOISE, SHEAR><<<dim3((a.nx + kStepBlock - 1) / kStepBlock, a.ny, a.nz_grid), block, 0, s>>>(a);
   } else {
-    const dim3 grid((a.nx / 2 + kStepBlock - 1) / kStepBlock, a.ny, a.nz);
+    const dim3 grid((a.nx / 2 + kStepBlock - 1) / kStepBlock, a.ny, a.nz_grid);
     // The general rates hold every central moment through the collision: their two-site
     // kernel gets a 168-register cap (three blocks per SM) instead of spilling.
     constexpr int kMinb = SHEAR ? 4 : 3;

@@ -17,13 +17,13 @@ template <int D, typename S, int PARITY, bool NOISE, bool SHEAR, bool ISO>
 __global__ void __launch_bounds__(kStepBlock) step_kernel(const StepArgs a) {
   const int x = blockIdx.x * kStepBlock + threadIdx.x;
   if (x >= a.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = blockIdx.y, z = blockIdx.z + a.z_lo;
   const Neighbourhood nb = neighbourhood(x, y, z, a.nx, a.ny, a.nz);
   S *__restrict__ f = static_cast<S *>(a.f);
 
   float F[3][3][3];
   load_logical<D, S, PARITY>(f, a.plane, nb, F);
-  const uint32_t site = (uint32_t)(x + (long long)a.nx * (y + (long long)a.ny * z));
+  const uint32_t site = (uint32_t)(x + (long long)a.nx * (y + (long long)a.ny * z)) + a.site_base;
   collide_tile<D, NOISE, float, false, SHEAR, ISO>(F, a.rho0, a.om, a.phc, site, a.step_lo, a.step_hi, a.ks0,
                                                    a.ks1);
   store_streamed<D, S, PARITY>(f, a.plane, nb, F);
@@ -33,12 +33,12 @@ template <int D, typename S, int PARITY, bool NOISE, bool ROLLED, bool SHEAR, in
 __global__ void __launch_bounds__(kStepBlock, MINB) step2_kernel(const StepArgs a) {
   const int x0 = 2 * (blockIdx.x * kStepBlock + threadIdx.x);
   if (x0 >= a.nx) return;
-  const Addr2 ad = addr2(x0, blockIdx.y, blockIdx.z, a.nx, a.ny, a.nz);
+  const Addr2 ad = addr2(x0, blockIdx.y, blockIdx.z + a.z_lo, a.nx, a.ny, a.nz);
   S *__restrict__ f = static_cast<S *>(a.f);
 
   float2 F[3][3][3];
   load_logical2<D, S, PARITY>(f, a.plane, ad, F);
-  collide_tile<D, NOISE, float2, ROLLED, SHEAR, ISO>(F, a.rho0, a.om, a.phc, (uint32_t)ad.s0, a.step_lo,
+  collide_tile<D, NOISE, float2, ROLLED, SHEAR, ISO>(F, a.rho0, a.om, a.phc, (uint32_t)ad.s0 + a.site_base, a.step_lo,
                                                      a.step_hi, a.ks0, a.ks1);
   store_streamed2<D, S, PARITY>(f, a.plane, ad, F);
 }
@@ -59,7 +59,7 @@ cudaError_t launch_kernel(int variant, const StepArgs &a, cudaStream_t s) {
     // 102 for D3Q27 (five blocks: more warps to hide latency, at the risk of spills) and
     // 51 for the lighter D2Q9 update (ten blocks).
     constexpr int kOcc = D == 3 ? 5 : 10;
-    const dim3 grid((a.nx / 2 + kStepBlock - 1) / kStepBlock, a.ny, a.nz);
+    const dim3 grid((a.nx / 2 + kStepBlock - 1) / kStepBlock, a.ny, a.nz_grid);
     const bool occ = variant == kStepPairOcc || variant == kStepPairRolledOcc;
     const bool rolled = !ISO && (variant == kStepPairRolled || variant == kStepPairRolledOcc);
     if (occ) {
@@ -74,7 +74,7 @@ cudaError_t launch_kernel(int variant, const StepArgs &a, cudaStream_t s) {
         step2_kernel<D, S, PARITY, NOISE, false, SHEAR, 4, ISO><<<grid, block, 0, s>>>(a);
     }
   } else {
-    const dim3 grid((a.nx + kStepBlock - 1) / kStepBlock, a.ny, a.nz);
+    const dim3 grid((a.nx + kStepBlock - 1) / kStepBlock, a.ny, a.nz_grid);
     step_kernel<D, S, PARITY, NOISE, SHEAR, ISO><<<grid, block, 0, s>>>(a);
   }
   return cudaGetLastError();

@@ -125,6 +125,26 @@ def _load():
         "flbm_batch_uses_graph": (ctypes.c_int, [vp]),
         "flbm_batch_sync": (ctypes.c_int, [vp]),
         "flbm_batch_test_wait_timeout": (ctypes.c_int, [vp, ctypes.c_uint32]),
+        "flbm_slab_required_bytes": (ctypes.c_size_t, [ctypes.c_int, i64p, ctypes.c_int64, ctypes.c_int]),
+        "flbm_create_slab": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, i64p, ctypes.c_int64, ctypes.c_int64,
+                                            dp, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_int, vp,
+                                            vp, ctypes.c_size_t]),
+        "flbm_slab_halo": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, i64p, i64p,
+                                          ctypes.POINTER(ctypes.c_int), i64p]),
+        "flbm_domain_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, i64p, dp, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int)]),
+        "flbm_domain_destroy": (None, [vp]),
+        "flbm_domain_size": (ctypes.c_int, [vp]),
+        "flbm_domain_slab": (vp, [vp, ctypes.c_int]),
+        "flbm_domain_init_uniform": (ctypes.c_int, [vp, dp, ctypes.c_double, ctypes.c_uint64]),
+        "flbm_domain_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "flbm_domain_get_step": (ctypes.c_int64, [vp]),
+        "flbm_domain_set_step_variant": (ctypes.c_int, [vp, ctypes.c_int]),
+        "flbm_domain_stats": (ctypes.c_int, [vp, ctypes.POINTER(flbm_stats_t)]),
+        "flbm_domain_get_populations": (ctypes.c_int, [vp, dp, ctypes.c_size_t]),
+        "flbm_domain_set_populations": (ctypes.c_int, [vp, dp, ctypes.c_size_t]),
+        "flbm_domain_sync": (ctypes.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -404,6 +424,97 @@ def flbm_batch_test_wait_timeout(b, polls):
     _check(_lib.flbm_batch_test_wait_timeout(b, int(polls)))
 
 
+def flbm_slab_required_bytes(lattice, dims, z_count, storage=FLBM_FP32):
+    return int(_lib.flbm_slab_required_bytes(int(lattice), _dims(dims), int(z_count), int(storage)))
+
+
+def flbm_create_slab(lattice, dims, z_begin, z_count, lam, kBT, rho0, seed, storage=FLBM_FP32, cuda_stream=None,
+                     dev_buf=None, dev_buf_bytes=0):
+    ctx = ctypes.c_void_p()
+    lam = _lambda(lattice, lam)
+    _check(_lib.flbm_create_slab(ctypes.byref(ctx), int(lattice), _dims(dims), int(z_begin), int(z_count), _dp(lam),
+                                 float(kBT), float(rho0), int(seed) & 0xFFFFFFFFFFFFFFFF, int(storage),
+                                 ctypes.c_void_p(cuda_stream) if cuda_stream else None,
+                                 ctypes.c_void_p(dev_buf) if dev_buf else None, int(dev_buf_bytes)))
+    return ctx
+
+
+def flbm_slab_halo(lattice, dims, z_count, phase, side):
+    """(send_offsets, recv_offsets, region_len) of one halo message, in elements."""
+    so = (ctypes.c_int64 * 9)()
+    ro = (ctypes.c_int64 * 9)()
+    n = ctypes.c_int(0)
+    ln = ctypes.c_int64(0)
+    _check(_lib.flbm_slab_halo(int(lattice), _dims(dims), int(z_count), int(phase), int(side), so, ro,
+                               ctypes.byref(n), ctypes.byref(ln)))
+    return [int(so[k]) for k in range(n.value)], [int(ro[k]) for k in range(n.value)], int(ln.value)
+
+
+def flbm_domain_create(lattice, dims, lam, kBT, rho0, seed, storage=FLBM_FP32, nslabs=2, devices=None):
+    d = ctypes.c_void_p()
+    lam = _lambda(lattice, lam)
+    devs = (ctypes.c_int * int(nslabs))(*[int(x) for x in devices]) if devices is not None else None
+    _check(_lib.flbm_domain_create(ctypes.byref(d), int(lattice), _dims(dims), _dp(lam), float(kBT), float(rho0),
+                                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(storage), int(nslabs), devs))
+    return d
+
+
+def flbm_domain_destroy(d):
+    _lib.flbm_domain_destroy(d)
+
+
+def flbm_domain_size(d):
+    return int(_lib.flbm_domain_size(d))
+
+
+def flbm_domain_slab(d, k):
+    ctx = _lib.flbm_domain_slab(d, int(k))
+    if not ctx:
+        raise FlbmError(FLBM_EINVAL, _lib.flbm_last_error().decode())
+    return ctypes.c_void_p(ctx)
+
+
+def flbm_domain_init_uniform(d, u0=(0.0, 0.0, 0.0), rho_perturb_amp=0.0, perturb_seed=0):
+    u = np.ascontiguousarray(np.asarray(list(u0) + [0.0] * (3 - len(u0)), dtype=np.float64))
+    _check(_lib.flbm_domain_init_uniform(d, _dp(u), float(rho_perturb_amp), int(perturb_seed)))
+
+
+def flbm_domain_step(d, n=1):
+    _check(_lib.flbm_domain_step(d, int(n)))
+
+
+def flbm_domain_get_step(d):
+    return int(_lib.flbm_domain_get_step(d))
+
+
+def flbm_domain_set_step_variant(d, variant):
+    _check(_lib.flbm_domain_set_step_variant(d, int(variant)))
+
+
+def flbm_domain_stats(d, allow_nonfinite=False):
+    out = flbm_stats_t()
+    st = _lib.flbm_domain_stats(d, ctypes.byref(out))
+    if not (st == FLBM_ENUMERIC and allow_nonfinite):
+        _check(st)
+    return out.to_dict()
+
+
+def flbm_domain_get_populations(d, lattice, dims):
+    q = Q_OF[lattice]
+    out = np.empty((q, int(dims[2]), int(dims[1]), int(dims[0])), dtype=np.float64)
+    _check(_lib.flbm_domain_get_populations(d, _dp(out), out.size))
+    return out
+
+
+def flbm_domain_set_populations(d, f):
+    arr = np.ascontiguousarray(np.asarray(f, dtype=np.float64))
+    _check(_lib.flbm_domain_set_populations(d, _dp(arr), arr.size))
+
+
+def flbm_domain_sync(d):
+    _check(_lib.flbm_domain_sync(d))
+
+
 # ---- a thin owner object over the same calls ---------------------------------------------
 class Lattice:
     """Owns one context; methods forward to the C ABI calls of the same name."""
@@ -549,6 +660,65 @@ class Batch:
                 if v is not None:
                     v.ctx = None
             flbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Domain:
+    """Owns a domain (flbm_domain_*): one lattice split along z into slabs."""
+
+    def __init__(self, lattice, dims, lam, kBT, rho0=1.0, seed=0, storage=FLBM_FP32, nslabs=2, devices=None):
+        self.lattice = int(lattice)
+        self.dims = tuple(int(x) for x in dims)
+        self.handle = flbm_domain_create(lattice, self.dims, lam, kBT, rho0, seed, storage, nslabs, devices)
+
+    def __len__(self):
+        return flbm_domain_size(self.handle)
+
+    def init_uniform(self, u0=(0.0, 0.0, 0.0), amp=0.0, perturb_seed=0):
+        flbm_domain_init_uniform(self.handle, u0, amp, perturb_seed)
+
+    def step(self, n=1):
+        flbm_domain_step(self.handle, n)
+
+    @property
+    def step_count(self):
+        return flbm_domain_get_step(self.handle)
+
+    @property
+    def variant(self):
+        return flbm_get_step_variant(flbm_domain_slab(self.handle, 0))
+
+    @variant.setter
+    def variant(self, v):
+        flbm_domain_set_step_variant(self.handle, v)
+
+    def stats(self, allow_nonfinite=False):
+        return flbm_domain_stats(self.handle, allow_nonfinite)
+
+    def populations(self):
+        return flbm_domain_get_populations(self.handle, self.lattice, self.dims)
+
+    def set_populations(self, f):
+        flbm_domain_set_populations(self.handle, f)
+
+    def sync(self):
+        flbm_domain_sync(self.handle)
+
+    def close(self):
+        if self.handle:
+            flbm_domain_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):
