@@ -164,11 +164,16 @@ void fill_args(flbm_ctx *c) {
   for (int v = 0; v < 27; ++v) {
     a.om[v] = 0.0f;
     a.phc[v] = 0.0f;
+    a.om_t[v] = 0.0f;
+    a.phc_t[v] = 0.0f;
   }
   for (int v = c->D + 1; v < c->Q; ++v) {
     const double L = c->lambda[v];
     a.om[v] = float(1.0 - L);
     a.phc[v] = float(std::sqrt(c->kBT * L * (2.0 - L) * mode_bnorm_lattice(c->lattice, v) * 3.0));
+    // Scales are powers of two: the products are exact.
+    a.om_t[v] = a.om[v] * mode_tile_scale(c->lattice, v);
+    a.phc_t[v] = a.phc[v] * mode_tile_scale(c->lattice, v);
   }
   // The paper's structure: rate 1 for every non-conserved mode except the shear modes
   // (isotropic variant: except the second-order modes 4-9).
@@ -849,8 +854,8 @@ int batch_params(flbm_batch *b) {
     L.om_shear = a.om[ref];
     L.phc_shear = a.phc[ref];
     for (int v = 0; v < 27; ++v) {
-      rates[size_t(i) * 54 + size_t(v)] = a.om[v];
-      rates[size_t(i) * 54 + 27 + size_t(v)] = a.phc[v];
+      rates[size_t(i) * 54 + size_t(v)] = a.om_t[v];  // the collision's (tile-scaled) constants
+      rates[size_t(i) * 54 + 27 + size_t(v)] = a.phc_t[v];
     }
     // The shear form needs the paper's structure and one rate shared by the shear modes.
     bool ok = c->shear;

@@ -82,6 +82,26 @@ __device__ __forceinline__ void shift_inv(T &k0, T &k1, T &k2, T u) {
   k1 = r1;
 }
 
+// The inverses in the halved convention: along the transformed axis the slots of order 1
+// and 2 hold half their moment (order 0 is whole). raw_inv_h takes (s, p1/2, p2/2) and
+// gives the three values, (v(+1), v(-1)) = (cs^2 s + p2 +- p1) / 2 and v(0) = s - cs^2 s - p2,
+// in 4 operations instead of 6; shift_inv_h keeps the convention (hu = u / 2).
+template <typename T>
+__device__ __forceinline__ void raw_inv_h(T &p0, T &p1, T &p2) {
+  const T s = p0;
+  const T e = vfma(splat<T>(0.5f * kCs2), s, p2);  // (cs^2 s + p2) / 2
+  p0 = vsub(e, p1);
+  p2 = vadd(e, p1);
+  p1 = vfma(splat<T>(-2.0f), e, s);
+}
+
+template <typename T>
+__device__ __forceinline__ void shift_inv_h(T &k0, T &k1, T &k2, T u, T hu) {
+  const T r1 = vfma(hu, k0, k1);   // (k1 + u k0) / 2
+  k2 = vfma(u, vadd(k1, r1), k2);  // (k2 + 2 u k1 + u^2 k0) / 2
+  k1 = r1;
+}
+
 // ---- tile transforms ---------------------------------------------------------------
 // Tile layout: F[z][y][x]; for D = 2 only the plane z = 1 is used.
 template <int D, typename T>
@@ -159,6 +179,49 @@ __device__ __forceinline__ void tile_shift_inv(T (&F)[3][3][3], T ux, T uy, T uz
   for (int z = z0; z < z1; ++z)
 #pragma unroll
     for (int b = 0; b < 3; ++b) shift_inv(F[z][b][0], F[z][b][1], F[z][b][2], ux);
+}
+
+// Inverses of the whole tile in the halved convention (tile_scale in lattice.cuh): central
+// moments scaled by 2^-(nonzero orders) -> raw moments (same scaling) -> populations.
+template <int D, typename T>
+__device__ __forceinline__ void tile_shift_inv_h(T (&F)[3][3][3], T ux, T uy, T uz) {
+  constexpr int z0 = (D == 3) ? 0 : 1, z1 = (D == 3) ? 3 : 2;
+  const T h = splat<T>(0.5f);
+  if (D == 3) {
+    const T huz = vmul(h, uz);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) shift_inv_h(F[0][b][a], F[1][b][a], F[2][b][a], uz, huz);
+  }
+  const T huy = vmul(h, uy), hux = vmul(h, ux);
+#pragma unroll
+  for (int z = z0; z < z1; ++z)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) shift_inv_h(F[z][0][a], F[z][1][a], F[z][2][a], uy, huy);
+#pragma unroll
+  for (int z = z0; z < z1; ++z)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) shift_inv_h(F[z][b][0], F[z][b][1], F[z][b][2], ux, hux);
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void tile_raw_inv_h(T (&F)[3][3][3]) {
+  constexpr int z0 = (D == 3) ? 0 : 1, z1 = (D == 3) ? 3 : 2;
+  if (D == 3) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) raw_inv_h(F[0][b][a], F[1][b][a], F[2][b][a]);
+  }
+#pragma unroll
+  for (int z = z0; z < z1; ++z)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) raw_inv_h(F[z][0][a], F[z][1][a], F[z][2][a]);
+#pragma unroll
+  for (int z = z0; z < z1; ++z)
+#pragma unroll
+    for (int y = 0; y < 3; ++y) raw_inv_h(F[z][y][0], F[z][y][1], F[z][y][2]);
 }
 
 // Moment (a, b, c) of the tile after the forward transforms (c = 0 for D = 2).
@@ -371,6 +434,75 @@ __device__ __forceinline__ void store_streamed2(S *__restrict__ f, long long pla
       }
 }
 
+// Pairs of the step kernels: on even steps (PARITY 0) lane x holds site x0 and lane y site
+// x0 + 1; on odd steps lane x holds x0 + 1 and lane y x0 + 2, which is the row's first site
+// when x0 + 2 = nx (ad.sp2). An odd step reads slot opposite(i) at x - c_i and writes slot i
+// at x + c_i, so with this pairing the populations with c_x = +-1 (18 of 27 on D3Q27) move as
+// aligned pairs, (x0, x0 + 1) or (x0 + 2, x0 + 3), and only those with c_x = 0 take two scalar
+// accesses. Every site of a row is still covered once.
+template <int D, typename S, int PARITY>
+__device__ __forceinline__ void load_pairs(const S *__restrict__ f, long long plane, const Addr2 &ad,
+                                           float2 (&F)[3][3][3]) {
+  if (PARITY == 0) {
+    load_logical2<D, S, 0>(f, plane, ad, F);
+    return;
+  }
+  constexpr int z0 = (D == 3) ? -1 : 0, z1 = (D == 3) ? 1 : 0;
+#pragma unroll
+  for (int dz = z0; dz <= z1; ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = Lat<D>::index(dx, dy, dz);
+        const S *b = f + opposite<D>(i) * plane + ad.dy[1 - dy] + ad.dz[1 - dz];  // row of x - c_i
+        float2 v;
+        if (dx == 0) {
+          v.x = Storage<S>::load(b + ad.s0 + 1);
+          v.y = Storage<S>::load(b + ad.sp2);
+        } else {
+          v = Storage2<S>::load(b + (dx == 1 ? ad.s0 : ad.sp2));
+        }
+        F[dz + 1][dy + 1][dx + 1] = v;
+      }
+}
+
+template <int D, typename S, int PARITY>
+__device__ __forceinline__ void store_pairs(S *__restrict__ f, long long plane, const Addr2 &ad,
+                                            const float2 (&F)[3][3][3]) {
+  if (PARITY == 0) {
+    store_streamed2<D, S, 0>(f, plane, ad, F);
+    return;
+  }
+  constexpr int z0 = (D == 3) ? -1 : 0, z1 = (D == 3) ? 1 : 0;
+#pragma unroll
+  for (int dz = z0; dz <= z1; ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = Lat<D>::index(dx, dy, dz);
+        S *b = f + i * plane + ad.dy[1 + dy] + ad.dz[1 + dz];  // row of x + c_i
+        const float2 v = F[dz + 1][dy + 1][dx + 1];
+        if (dx == 0) {
+          Storage<S>::store(b + ad.s0 + 1, v.x);
+          Storage<S>::store(b + ad.sp2, v.y);
+        } else {
+          Storage2<S>::store(b + (dx == 1 ? ad.sp2 : ad.s0), v);
+        }
+      }
+}
+
+// Site index of a pair's lane x and the step from it to lane y (the pairing of load_pairs).
+template <int PARITY>
+__device__ __forceinline__ uint32_t pair_site0(const Addr2 &ad) {
+  return (uint32_t)(PARITY == 0 ? ad.s0 : ad.s0 + 1);
+}
+template <int PARITY>
+__device__ __forceinline__ uint32_t pair_dsite(const Addr2 &ad) {
+  return PARITY == 0 ? 1u : (uint32_t)(ad.sp2 - ad.s0 - 1);
+}
+
 // Raw moments of the deviation tile and rho, u (Eq. macro); entry (0,0,0) stays rho - rho0.
 template <int D, typename T>
 __device__ __forceinline__ void site_macros(T (&F)[3][3][3], float rho0, T &drho, T &rho, T &ux, T &uy,
@@ -378,12 +510,41 @@ __device__ __forceinline__ void site_macros(T (&F)[3][3][3], float rho0, T &drho
   tile_raw_fwd<D>(F);
   drho = mom<D>(F, 0, 0, 0);
   rho = vadd(splat<T>(rho0), drho);
-  T inv_rho;
-#pragma unroll
-  for (int l = 0; l < Lanes<T>::n; ++l) set_lane(inv_rho, l, 1.0f / lane(rho, l));
+  const T inv_rho = rcp_fast_lanes(rho);
   ux = vmul(mom<D>(F, 1, 0, 0), inv_rho);
   uy = vmul(mom<D>(F, 0, 1, 0), inv_rho);
   uz = (D == 3) ? vmul(mom<D>(F, 0, 0, 1), inv_rho) : splat<T>(0.0f);
+}
+
+// D3Q27 with the paper's rate structure needs only rho, j and the three mixed raw second
+// moments (shear modes, Sec. II-C). Per-axis sums and first moments of the deviation tile
+// (three passes that skip every second-order output): drho = sum d, j, and
+// P = (P_xy, P_xz, P_yz) = sum (cx cy, cx cz, cy cz) d. The tile is left partly reduced.
+template <typename T>
+__device__ __forceinline__ void shear_raw_moments(T (&F)[3][3][3], T &drho, T (&j)[3], T (&P)[3]) {
+  T r0[3][3], r1[3][3];  // [z][y]: sum over x, first moment in x
+#pragma unroll
+  for (int z = 0; z < 3; ++z)
+#pragma unroll
+    for (int y = 0; y < 3; ++y) {
+      r0[z][y] = vadd(F[z][y][1], vadd(F[z][y][0], F[z][y][2]));
+      r1[z][y] = vsub(F[z][y][2], F[z][y][0]);
+    }
+  T q00[3], q01[3], q10[3], q11[3];  // [z]: (x order, y order) = 00, 01 (c_y), 10 (c_x), 11 (c_x c_y)
+#pragma unroll
+  for (int z = 0; z < 3; ++z) {
+    q00[z] = vadd(r0[z][1], vadd(r0[z][0], r0[z][2]));
+    q01[z] = vsub(r0[z][2], r0[z][0]);
+    q10[z] = vadd(r1[z][1], vadd(r1[z][0], r1[z][2]));
+    q11[z] = vsub(r1[z][2], r1[z][0]);
+  }
+  drho = vadd(q00[1], vadd(q00[0], q00[2]));
+  j[2] = vsub(q00[2], q00[0]);
+  j[0] = vadd(q10[1], vadd(q10[0], q10[2]));
+  P[1] = vsub(q10[2], q10[0]);  // c_x c_z
+  j[1] = vadd(q01[1], vadd(q01[0], q01[2]));
+  P[2] = vsub(q01[2], q01[0]);  // c_y c_z
+  P[0] = vadd(q11[1], vadd(q11[0], q11[2]));  // c_x c_y
 }
 
 // Forward part shared by the step and the statistics: raw moments of the deviation
@@ -409,6 +570,17 @@ __device__ __forceinline__ void iso_rotate(T &a, T &b, T &c) {  // (k4, k5, k6) 
   a = vadd(s, c);
   b = d1;
   c = d2;
+}
+// iso_unrotate, each output halved (the halved convention of the inverse transforms).
+template <typename T>
+__device__ __forceinline__ void iso_unrotate_h(T &a, T &b, T &c) {
+  const T s4 = vmul(splat<T>(1.0f / 12.0f), vfma(splat<T>(2.0f), a, c));  // (k4 + k5) / 4
+  const T k6 = vmul(splat<T>(1.0f / 6.0f), vsub(a, c));                   // k6 / 2
+  const T k4 = vfma(splat<T>(0.25f), b, s4);   // ((k4 + k5) + (k4 - k5)) / 4
+  const T k5 = vfma(splat<T>(-0.25f), b, s4);
+  a = k4;
+  b = k5;
+  c = k6;
 }
 template <typename T>
 __device__ __forceinline__ void iso_unrotate(T &a, T &b, T &c) {  // (M4', M5', M6') -> (k4, k5, k6)

@@ -7,7 +7,9 @@
 // with I~_v = 1 exactly for the non-conserved modes v > D and the conserved modes
 // relaxed at rate 1 (k*_0 = rho, k*_1..D = 0), as the paper fixes in Sec. II-B and II-C.
 // The caller passes om_v = 1 - L_v and phc_v = sqrt(kBT L_v (2 - L_v) b_v / cs^2)
-// (host-computed), so phi_v = sqrt(rho) phc_v uses the local density.
+// (host-computed), so phi_v = sqrt(rho) phc_v uses the local density; both come multiplied
+// by the mode's tile scale (lattice.cuh, tile_scale), because the inverse transforms take
+// the post-collision moments in the halved convention of cm.cuh.
 // Noise: mode v uses normal n = v - D - 1 of block n / 4 of the site's Philox stream.
 // On return the tile holds the post-collision deviations d*_i = f*_i - w_i rho0.
 #pragma once
@@ -18,8 +20,8 @@
 namespace flbm {
 
 // ---- relaxation rates and noise amplitudes, as the collision reads them --------------
-// ArrayRates: om_v = 1 - L_v and phc_v = sqrt(kBT L_v (2 - L_v) b_v / cs^2) per mode, from
-// a kernel-argument array (constant bank).
+// ArrayRates: om_v = 1 - L_v and phc_v = sqrt(kBT L_v (2 - L_v) b_v / cs^2) per mode, times
+// the mode's tile scale, from a kernel-argument array (constant bank; host-computed).
 struct ArrayRates {
   const float *om_, *phc_;
   __device__ __forceinline__ float om(int v) const { return om_[v]; }
@@ -46,14 +48,15 @@ __host__ __device__ constexpr float noise_unit(int v) {
 // rate): om = 0 and phc_v = sqrt(kBT) sqrt(3 b_v) off the shear modes, om_sh and phc_sh
 // on them. phc_sh is the amplitude of a shear mode with b = 1/9 (D3Q27 v = 7..9, D2Q9
 // v = 5); D2Q9 mode 4 has b = 4/9 and so twice that amplitude (an exact scaling). Three
-// numbers per lattice.
+// numbers per lattice; the tile scales are compile-time factors.
 template <int D>
 struct ShearRates {
   float sqrt_kbt, om_sh, phc_sh;
   __device__ __forceinline__ static bool is_shear(int v) { return D == 3 ? (v >= 7 && v <= 9) : (v == 4 || v == 5); }
-  __device__ __forceinline__ float om(int v) const { return is_shear(v) ? om_sh : 0.0f; }
+  __device__ __forceinline__ float om(int v) const { return is_shear(v) ? om_sh * tile_scale<D>(v) : 0.0f; }
   __device__ __forceinline__ float phc(int v) const {
-    return is_shear(v) ? ((D == 2 && v == 4) ? 2.0f * phc_sh : phc_sh) : sqrt_kbt * noise_unit<D>(v);
+    return is_shear(v) ? ((D == 2 && v == 4) ? 2.0f * tile_scale<D>(v) : tile_scale<D>(v)) * phc_sh
+                       : sqrt_kbt * (noise_unit<D>(v) * tile_scale<D>(v));
   }
 };
 
@@ -95,23 +98,36 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
                                               uint32_t dsite = 1) {
   static_assert(!ISO || D == 3, "the isotropic variant is a D3Q27 basis");
   T drho, rho, ux, uy, uz;
-  if (SHEAR) {
+  T Pm[3];  // D3Q27, paper structure: raw P_xy, P_xz, P_yz
+  if (SHEAR && D == 3 && !ISO) {
+    T jv[3];
+    shear_raw_moments(F, drho, jv, Pm);
+    rho = vadd(splat<T>(rho0), drho);
+    const T inv_rho = rcp_fast_lanes(rho);
+    ux = vmul(jv[0], inv_rho);
+    uy = vmul(jv[1], inv_rho);
+    uz = vmul(jv[2], inv_rho);
+    mom<D>(F, 0, 0, 0) = rho;  // k*_0 = rho for the way back
+  } else if (SHEAR) {
     site_macros<D>(F, rho0, drho, rho, ux, uy, uz);
     mom<D>(F, 0, 0, 0) = rho;  // k*_0 = rho for the way back
+    if (D == 3) {
+      Pm[0] = F[0][1][1];
+      Pm[1] = F[1][0][1];
+      Pm[2] = F[1][1][0];
+    }
   } else {
     site_central_moments<D>(F, rho0, drho, rho, ux, uy, uz);
   }
-  T srho;
-#pragma unroll
-  for (int l = 0; l < Lanes<T>::n; ++l) set_lane(srho, l, sqrtf(lane(rho, l)));
+  const T srho = sqrt_fast_lanes(rho);
   if (D == 3) {
     if (SHEAR) {
       // raw (1,1,0), (1,0,1), (0,1,1) -> central; every other non-conserved mode restarts
       // from k^eq = 0 (ISO: also the normal stresses, rotated).
       const T nrho = vmul(splat<T>(-1.0f), rho);
-      const T kxy = vfma(vmul(nrho, ux), uy, F[0][1][1]);
-      const T kxz = vfma(vmul(nrho, ux), uz, F[1][0][1]);
-      const T kyz = vfma(vmul(nrho, uy), uz, F[1][1][0]);
+      const T kxy = vfma(vmul(nrho, ux), uy, Pm[0]);
+      const T kxz = vfma(vmul(nrho, ux), uz, Pm[1]);
+      const T kyz = vfma(vmul(nrho, uy), uz, Pm[2]);
       T kxx, kyy, kzz;
       if (ISO) {
         kxx = vfma(vmul(nrho, ux), ux, F[0][0][2]);
@@ -170,7 +186,7 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
         }
       }
     }
-    if (ISO) iso_unrotate(F[0][0][2], F[0][2][0], F[2][0][0]);
+    if (ISO) iso_unrotate_h(F[0][0][2], F[0][2][0], F[2][0][0]);
     F[0][0][1] = splat<T>(0.0f);  // k*_1 (x momentum, central)
     F[0][1][0] = splat<T>(0.0f);  // k*_2
     F[1][0][0] = splat<T>(0.0f);  // k*_3
@@ -215,20 +231,22 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
     F[1][0][1] = splat<T>(0.0f);  // k*_1
     F[1][1][0] = splat<T>(0.0f);  // k*_2
   }
-  // r* = N^{-1} k* (entry (0,0,0) = k*_0 = rho), then d* = M^{-1} r* - w rho0.
-  tile_shift_inv<D>(F, ux, uy, uz);
+  // r* = N^{-1} k* (entry (0,0,0) = k*_0 = rho), then d* = M^{-1} r* - w rho0, on the tile
+  // in the halved convention (every other entry already carries its tile scale).
+  tile_shift_inv_h<D>(F, ux, uy, uz);
   mom<D>(F, 0, 0, 0) = drho;
-  tile_raw_inv<D>(F);
+  tile_raw_inv_h<D>(F);
 }
 
 // The collision with per-mode arrays om_v, phc_v (kernel arguments).
+// dsite: site index of a pair's lane y minus that of lane x (1, or 1 - nx across a row's end).
 template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false, bool ISO = false>
 __device__ __forceinline__ void collide_tile(T (&F)[3][3][3], float rho0, const float *om,
                                              const float *phc, uint32_t site0, uint32_t step_lo,
                                              uint32_t step_hi, const uint32_t *ks0,
-                                             const uint32_t *ks1) {
+                                             const uint32_t *ks1, uint32_t dsite = 1) {
   collide_rates<D, NOISE, T, ROLLED, SHEAR, ISO>(F, rho0, ArrayRates{om, phc}, site0, step_lo, step_hi,
-                                            KeyTable{ks0, ks1});
+                                            KeyTable{ks0, ks1}, dsite);
 }
 
 }  // namespace flbm

@@ -113,15 +113,67 @@ __device__ __forceinline__ void store19_2(S *__restrict__ f, long long plane, co
       }
 }
 
+// The pairing of load_pairs / store_pairs (cm.cuh): on odd steps lanes hold x0 + 1 and x0 + 2,
+// so the populations with c_x = +-1 (10 of 19) move as aligned pairs.
+template <typename S, int PARITY>
+__device__ __forceinline__ void load19_pairs(const S *__restrict__ f, long long plane, const Addr2 &ad,
+                                             float2 (&F)[19]) {
+  if (PARITY == 0) {
+    load19_2<S, 0>(f, plane, ad, F);
+    return;
+  }
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!d3q19_has(dx, dy, dz)) continue;
+        const int i = Lat<3>::index(dx, dy, dz);
+        const S *b = f + opposite<3>(i) * plane + ad.dy[1 - dy] + ad.dz[1 - dz];
+        float2 v;
+        if (dx == 0) {
+          v.x = Storage<S>::load(b + ad.s0 + 1);
+          v.y = Storage<S>::load(b + ad.sp2);
+        } else {
+          v = Storage2<S>::load(b + (dx == 1 ? ad.s0 : ad.sp2));
+        }
+        F[i] = v;
+      }
+}
+template <typename S, int PARITY>
+__device__ __forceinline__ void store19_pairs(S *__restrict__ f, long long plane, const Addr2 &ad,
+                                              const float2 (&F)[19]) {
+  if (PARITY == 0) {
+    store19_2<S, 0>(f, plane, ad, F);
+    return;
+  }
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!d3q19_has(dx, dy, dz)) continue;
+        const int i = Lat<3>::index(dx, dy, dz);
+        S *b = f + i * plane + ad.dy[1 + dy] + ad.dz[1 + dz];
+        const float2 v = F[i];
+        if (dx == 0) {
+          Storage<S>::store(b + ad.s0 + 1, v.x);
+          Storage<S>::store(b + ad.sp2, v.y);
+        } else {
+          Storage2<S>::store(b + (dx == 1 ? ad.sp2 : ad.s0), v);
+        }
+      }
+}
+
 // rho, u and the raw moments of the deviations (r_0 = rho - rho0).
 template <typename T>
 __device__ __forceinline__ void d3q19_macros(const T (&F)[19], float rho0, T (&r)[19], T &rho, T &ux, T &uy,
                                              T &uz) {
   d3q19_raw(F, r);
   rho = vadd(splat<T>(rho0), r[0]);
-  T inv_rho;
-#pragma unroll
-  for (int l = 0; l < Lanes<T>::n; ++l) set_lane(inv_rho, l, 1.0f / lane(rho, l));
+  const T inv_rho = rcp_fast_lanes(rho);
   ux = vmul(r[1], inv_rho);
   uy = vmul(r[2], inv_rho);
   uz = vmul(r[3], inv_rho);
@@ -132,7 +184,7 @@ __device__ __forceinline__ void d3q19_macros(const T (&F)[19], float rho0, T (&r
 // formed. om_v = 1 - Lambda_v, phc_v = sqrt(kBT Lambda_v (2 - Lambda_v) b_v / cs^2).
 template <bool NOISE, typename T, bool SHEAR, typename K>
 __device__ __forceinline__ void collide19(T (&F)[19], float rho0, const float *om, const float *phc, uint32_t site0,
-                                          uint32_t step_lo, uint32_t step_hi, const K &keys) {
+                                          uint32_t step_lo, uint32_t step_hi, const K &keys, uint32_t dsite = 1) {
   T r[19], rho, ux, uy, uz;
   d3q19_macros(F, rho0, r, rho, ux, uy, uz);
   const T jx = r[1], jy = r[2], jz = r[3], drho = r[0];
@@ -150,13 +202,11 @@ __device__ __forceinline__ void collide19(T (&F)[19], float rho0, const float *o
     for (int v = 4; v < 19; ++v) r[v] = vmul(splat<T>(om[v]), r[v]);
   }
   if (NOISE) {
-    T srho;
-#pragma unroll
-    for (int l = 0; l < Lanes<T>::n; ++l) set_lane(srho, l, sqrtf(lane(rho, l)));
+    const T srho = sqrt_fast_lanes(rho);
 #pragma unroll
     for (int blk = 0; blk < 4; ++blk) {
       T z[4];
-      normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, keys, srho, z);
+      normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, keys, srho, z, dsite);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int v = 4 + 4 * blk + j;

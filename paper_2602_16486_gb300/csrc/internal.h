@@ -30,6 +30,8 @@ struct StepArgs {
   int *status;        // device word: nonzero after a bounded wait gave up (pipelined kernel)
   float om[27];       // 1 - Lambda_v (conserved modes: unused)
   float phc[27];      // sqrt(kBT Lambda_v (2 - Lambda_v) b_v / cs^2); phi_v = sqrt(rho) phc_v
+  float om_t[27];     // om and phc times the mode's tile scale (lattice.cuh, tile_scale): the
+  float phc_t[27];    // constants the D2Q9 / D3Q27 collision takes (isotropic modes 4-6: 1)
 };
 
 // ---- batched ensembles (batch.cu) ----------------------------------------------------
@@ -134,6 +136,8 @@ cudaError_t launch_gather_sites(int D, int storage, int parity, const void *f, l
 double mode_bnorm(int D, int v);
 // b_v of the lattice's basis (lattice 2: the isotropic D3Q27 variant, modes 4-6 rotated).
 double mode_bnorm_lattice(int lattice, int v);
+// Tile scale of mode v of a public lattice (1 for D3Q19, whose collision has no tile).
+float mode_tile_scale(int lattice, int v);
 size_t storage_bytes(int storage);
 
 }  // namespace flbm

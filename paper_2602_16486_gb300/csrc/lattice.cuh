@@ -151,4 +151,17 @@ __host__ __device__ constexpr int d2q9_mode_tensor(int v) {
   return v == 0 ? 0 : v == 1 ? 1 : v == 2 ? 3 : v == 5 ? 4 : v == 6 ? 5 : v == 7 ? 7 : v == 8 ? 8 : -1;
 }
 
+// Scale of mode v in the tile the inverse transforms take (cm.cuh, tile_shift_inv_h and
+// tile_raw_inv_h): 2^-n, n the number of axes along which the mode has a nonzero order.
+// The collision writes k*_v times this scale, so that the 1/2 of every 3-point inverse
+// is folded into its constants. D2Q9 modes 3 and 4 combine (2,0) and (0,2): 1/2.
+__host__ __device__ constexpr int nonzero_orders(int t) {
+  return (t % 3 != 0 ? 1 : 0) + ((t / 3) % 3 != 0 ? 1 : 0) + (t / 9 != 0 ? 1 : 0);
+}
+template <int D>
+__host__ __device__ constexpr float tile_scale(int v) {
+  return D == 3 ? 1.0f / float(1 << nonzero_orders(d3q27_mode_tensor(v)))
+                : (v == 0 ? 1.0f : (v <= 4 ? 0.5f : 0.25f));
+}
+
 }  // namespace flbm

@@ -222,6 +222,12 @@ double mode_bnorm_lattice(int lattice, int v) {
   return mode_bnorm(lattice == 0 ? 2 : 3, v);
 }
 
+float mode_tile_scale(int lattice, int v) {
+  if (lattice == 3) return 1.0f;
+  if (lattice == 2 && v >= 4 && v <= 6) return 1.0f;  // rotated; halved after the rotation back
+  return lattice == 0 ? tile_scale<2>(v) : tile_scale<3>(v);
+}
+
 double mode_bnorm(int D, int v) {
   const double b1[3] = {1.0, 1.0 / 3.0, 2.0 / 9.0};
   if (D == 3) {

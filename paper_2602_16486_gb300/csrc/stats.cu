@@ -41,7 +41,7 @@ __device__ __forceinline__ void pair_columns19(const S *__restrict__ f, long lon
     if (valid[0]) {
       const uint32_t r = (uint32_t)s / (uint32_t)nx, q = r / (uint32_t)ny;
       const int x0 = (int)((uint32_t)s - r * (uint32_t)nx), y = (int)(r - q * (uint32_t)ny), z = (int)q;
-      load19_2<S, PARITY>(f, plane, addr2(x0, y, z, nx, ny, nz), F);
+      load19_pairs<S, PARITY>(f, plane, addr2(x0, y, z, nx, ny, nz), F);
     } else {
 #pragma unroll
       for (int a = 0; a < 19; ++a) F[a] = make_float2(0.0f, 0.0f);
@@ -91,7 +91,8 @@ __device__ __forceinline__ void pair_columns19(const S *__restrict__ f, long lon
 }
 
 // Columns of the two sites of a pair (lane x: site s, lane y: site s + 1). PAIRROW: nx is
-// even, so s (even) and s + 1 share a row and load as pairs (cm.cuh, load_logical2).
+// even, so s (even) and s + 1 share a row and load as pairs; on odd parity the pair is the
+// step's (cm.cuh, load_pairs: sites s + 1 and s + 2 of the row), which covers the same sites.
 template <int D, typename S, int PARITY, bool PAIRROW, bool ISO>
 __device__ __forceinline__ void pair_columns(const S *__restrict__ f, long long plane, int nx, int ny, int nz,
                                              float rho0, long long s, long long N,
@@ -102,7 +103,7 @@ __device__ __forceinline__ void pair_columns(const S *__restrict__ f, long long 
     if (valid[0]) {
       const uint32_t r = (uint32_t)s / (uint32_t)nx, q = r / (uint32_t)ny;
       const int x0 = (int)((uint32_t)s - r * (uint32_t)nx), y = (int)(r - q * (uint32_t)ny), z = (int)q;
-      load_logical2<D, S, PARITY>(f, plane, addr2(x0, y, z, nx, ny, nz), F);
+      load_pairs<D, S, PARITY>(f, plane, addr2(x0, y, z, nx, ny, nz), F);
     } else {
 #pragma unroll
       for (int a = 0; a < 27; ++a) (&F[0][0][0])[a] = make_float2(0.0f, 0.0f);

@@ -31,10 +31,10 @@ __global__ void __launch_bounds__(kStepBlock, MINB) step19_2_kernel(const StepAr
   const Addr2 ad = addr2(x0, blockIdx.y, blockIdx.z + a.z_lo, a.nx, a.ny, a.nz);
   S *__restrict__ f = static_cast<S *>(a.f);
   float2 F[19];
-  load19_2<S, PARITY>(f, a.plane, ad, F);
-  collide19<NOISE, float2, SHEAR>(F, a.rho0, a.om, a.phc, (uint32_t)ad.s0 + a.site_base, a.step_lo, a.step_hi,
-                                  KeyTable{a.ks0, a.ks1});
-  store19_2<S, PARITY>(f, a.plane, ad, F);
+  load19_pairs<S, PARITY>(f, a.plane, ad, F);
+  collide19<NOISE, float2, SHEAR>(F, a.rho0, a.om, a.phc, pair_site0<PARITY>(ad) + a.site_base, a.step_lo,
+                                  a.step_hi, KeyTable{a.ks0, a.ks1}, pair_dsite<PARITY>(ad));
+  store19_pairs<S, PARITY>(f, a.plane, ad, F);
 }
 
 template <typename S, int PARITY, bool NOISE, bool SHEAR>

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kStepBlock) step_kernel(const StepArgs a) {
   float F[3][3][3];
   load_logical<D, S, PARITY>(f, a.plane, nb, F);
   const uint32_t site = (uint32_t)(x + (long long)a.nx * (y + (long long)a.ny * z)) + a.site_base;
-  collide_tile<D, NOISE, float, false, SHEAR, ISO>(F, a.rho0, a.om, a.phc, site, a.step_lo, a.step_hi, a.ks0,
+  collide_tile<D, NOISE, float, false, SHEAR, ISO>(F, a.rho0, a.om_t, a.phc_t, site, a.step_lo, a.step_hi, a.ks0,
                                                    a.ks1);
   store_streamed<D, S, PARITY>(f, a.plane, nb, F);
 }
@@ -37,10 +37,10 @@ __global__ void __launch_bounds__(kStepBlock, MINB) step2_kernel(const StepArgs 
   S *__restrict__ f = static_cast<S *>(a.f);
 
   float2 F[3][3][3];
-  load_logical2<D, S, PARITY>(f, a.plane, ad, F);
-  collide_tile<D, NOISE, float2, ROLLED, SHEAR, ISO>(F, a.rho0, a.om, a.phc, (uint32_t)ad.s0 + a.site_base, a.step_lo,
-                                                     a.step_hi, a.ks0, a.ks1);
-  store_streamed2<D, S, PARITY>(f, a.plane, ad, F);
+  load_pairs<D, S, PARITY>(f, a.plane, ad, F);
+  collide_tile<D, NOISE, float2, ROLLED, SHEAR, ISO>(F, a.rho0, a.om_t, a.phc_t, pair_site0<PARITY>(ad) + a.site_base,
+                                                     a.step_lo, a.step_hi, a.ks0, a.ks1, pair_dsite<PARITY>(ad));
+  store_pairs<D, S, PARITY>(f, a.plane, ad, F);
 }
 
 template <typename S>

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 2) step_pipe_kernel(const Ste
       fetch_tile<D, S, PARITY>(f, a.plane, nx, ny, nz, r + 2 * stride, st, &bars[s], lane);
     const int y = (int)(r % ny), z = (int)(r / ny);
     const Addr2 ad = addr2(x0, y, z, nx, ny, nz);
-    collide_tile<D, NOISE, float2, true, SHEAR>(F, a.rho0, a.om, a.phc, (uint32_t)ad.s0, a.step_lo,
+    collide_tile<D, NOISE, float2, true, SHEAR>(F, a.rho0, a.om_t, a.phc_t, (uint32_t)ad.s0, a.step_lo,
                                                 a.step_hi, a.ks0, a.ks1);
     store_streamed2<D, S, PARITY>(f, a.plane, ad, F);
   }

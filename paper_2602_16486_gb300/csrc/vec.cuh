@@ -80,4 +80,23 @@ __device__ __forceinline__ void set_lane(float2 &v, int l, float x) {
     v.y = x;
 }
 
+// 1 / x and sqrt(x) of each lane by the hardware approximations (PTX rcp.approx.ftz and
+// sqrt.approx.ftz: within about one unit in the last place for the positive normal
+// densities the step sees), instead of the IEEE-rounded division and square root, whose
+// refinement and special-case paths cost several instructions per lane.
+__device__ __forceinline__ float rcp_fast(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_fast(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_fast_lanes(float x) { return rcp_fast(x); }
+__device__ __forceinline__ float2 rcp_fast_lanes(float2 x) { return make_float2(rcp_fast(x.x), rcp_fast(x.y)); }
+__device__ __forceinline__ float sqrt_fast_lanes(float x) { return sqrt_fast(x); }
+__device__ __forceinline__ float2 sqrt_fast_lanes(float2 x) { return make_float2(sqrt_fast(x.x), sqrt_fast(x.y)); }
+
 }  // namespace flbm
