@@ -34,7 +34,9 @@ struct Storage<float> {
 };
 template <>
 struct Storage<__nv_bfloat16> {
-  __device__ __forceinline__ static float load(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+  __device__ __forceinline__ static float load(const __nv_bfloat16 *p) {
+    return __uint_as_float((uint32_t)(*reinterpret_cast<const unsigned short *>(p)) << 16);
+  }
   __device__ __forceinline__ static void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 template <>
@@ -330,7 +332,9 @@ struct Storage2<float> {
 template <>
 struct Storage2<__nv_bfloat16> {
   __device__ __forceinline__ static float2 load(const __nv_bfloat16 *p) {
-    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    // bf16 is the top half of an FP32 word: two bit operations per pair.
+    const uint32_t x = *reinterpret_cast<const uint32_t *>(p);
+    return make_float2(__uint_as_float(x << 16), __uint_as_float(x & 0xFFFF0000u));
   }
   __device__ __forceinline__ static void store(__nv_bfloat16 *p, float2 v) {
     *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);

@@ -119,7 +119,6 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
   } else {
     site_central_moments<D>(F, rho0, drho, rho, ux, uy, uz);
   }
-  const T srho = sqrt_fast_lanes(rho);
   if (D == 3) {
     if (SHEAR) {
       // raw (1,1,0), (1,0,1), (0,1,1) -> central; every other non-conserved mode restarts
@@ -161,7 +160,7 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
 #pragma unroll 1
       for (int blk = 0; blk < 6; ++blk) {
         T z[4];
-        normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, keys, srho, z, dsite);
+        normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, keys, rho, z, dsite);
         switch (blk) {  // block-uniform branch: modes 4 + 4 blk .. 7 + 4 blk
           case 0: add_noise_block<0>(F, rates, z); break;
           case 1: add_noise_block<1>(F, rates, z); break;
@@ -175,7 +174,7 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
 #pragma unroll
       for (int blk = 0; blk < 6; ++blk) {
         T z[4];
-        normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, keys, srho, z, dsite);
+        normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, keys, rho, z, dsite);
         switch (blk) {
           case 0: add_noise_block<0>(F, rates, z); break;
           case 1: add_noise_block<1>(F, rates, z); break;
@@ -212,8 +211,8 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
     }
     if (NOISE) {
       T z0[4], z1[4];
-      normals4_scaled<T>(site0, step_lo, step_hi, 0u, keys, srho, z0, dsite);
-      normals4_scaled<T>(site0, step_lo, step_hi, 1u, keys, srho, z1, dsite);
+      normals4_scaled<T>(site0, step_lo, step_hi, 0u, keys, rho, z0, dsite);
+      normals4_scaled<T>(site0, step_lo, step_hi, 1u, keys, rho, z1, dsite);
       k3 = vfma(splat<T>(rates.phc(3)), z0[0], k3);
       k4 = vfma(splat<T>(rates.phc(4)), z0[1], k4);
       k5 = vfma(splat<T>(rates.phc(5)), z0[2], k5);

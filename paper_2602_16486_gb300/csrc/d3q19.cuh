@@ -202,11 +202,10 @@ __device__ __forceinline__ void collide19(T (&F)[19], float rho0, const float *o
     for (int v = 4; v < 19; ++v) r[v] = vmul(splat<T>(om[v]), r[v]);
   }
   if (NOISE) {
-    const T srho = sqrt_fast_lanes(rho);
-#pragma unroll
+  #pragma unroll
     for (int blk = 0; blk < 4; ++blk) {
       T z[4];
-      normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, keys, srho, z, dsite);
+      normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, keys, rho, z, dsite);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int v = 4 + 4 * blk + j;

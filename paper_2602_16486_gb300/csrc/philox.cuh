@@ -63,11 +63,11 @@ __device__ __forceinline__ uint4 philox4x32_10_ks(uint4 ctr, const K &keys) {
 }
 
 // Box-Muller, angle: cos and sin of 2 pi u_b depend only on u_b mod 1, and the word read
-// as a signed integer gives exactly that residue in [-1/2, 1/2): (int)w_b >> 9 is m - 2^23
-// when the top bit of w_b is set, m otherwise. So theta = ((int)w_b >> 9 + 1/2) 2 pi 2^-23
-// lies in (-pi, pi) (one FMA on an exactly converted integer) and cos / sin come from the
-// hardware approximations (__sincosf; absolute error about 4e-7 on [-pi, pi]), which cost
-// two instructions instead of a polynomial.
+// as a signed integer s_b is that residue times 2^32: u_b = (floor(s_b / 2^9) + 1/2) 2^-23
+// mod 1. The angle is taken as 2 pi (s_b 2^-32 + 2^-24), with s_b converted to FP32 (rounded to
+// 24 bits), which lies within pi 2^-23 (3.7e-7 rad) of 2 pi u_b: one conversion and one FMA,
+// in (-pi, pi]. cos / sin come from the hardware approximations (__sincosf; absolute error
+// about 4e-7 on [-pi, pi]), which cost two instructions instead of a polynomial.
 //
 // The radius: u_a = (2 m_a + 1) 2^-24 with y = 2 m_a + 1 an odd integer below 2^24, so
 // -2 ln u_a = -2 (ln y - 24 ln 2). y converts to FP32 exactly; the argument reduction
@@ -77,14 +77,15 @@ __device__ __forceinline__ uint4 philox4x32_10_ks(uint4 ctr, const K &keys) {
 // so the result keeps its relative accuracy as u_a -> 1, where r -> 0 (a hardware
 // logarithm has an absolute error there that exceeds the value). Checked against the FP64
 // definition over all 2^23 codes: relative error of -2 ln u_a below 3e-7.
-constexpr float kAngleScale = 0x1p-23f * 6.28318530717958647692f;  // 2 pi 2^-23
-constexpr float kAngleOffset = 0x1p-23f * 3.14159265358979323846f;  // pi 2^-23
+constexpr float kAngleScale = 0x1p-32f * 6.28318530717958647692f;  // 2 pi 2^-32
+constexpr float kAngleOffset = 0x1p-23f * 3.14159265358979323846f;  // pi 2^-23 = 2 pi 2^-24
 
 // Four normals of Philox block `blk` for each lane's site (lane l: site0 + l * dsite),
-// each multiplied by `scale` of its lane (the caller's sqrt(rho)).
+// each multiplied by sqrt(rho) of its lane: the radius is taken as sqrt(-2 rho ln u_a)
+// (hardware square root, PTX sqrt.approx.ftz) in one product and one root per lane.
 template <typename T, typename K>
 __device__ __forceinline__ void normals4_scaled(uint32_t site0, uint32_t step_lo, uint32_t step_hi,
-                                                uint32_t blk, const K &keys, T scale, T (&z)[4],
+                                                uint32_t blk, const K &keys, T rho, T (&z)[4],
                                                 uint32_t dsite = 1) {
   constexpr int L = Lanes<T>::n;
   float ang[L][2];
@@ -94,18 +95,21 @@ __device__ __forceinline__ void normals4_scaled(uint32_t site0, uint32_t step_lo
     const uint4 w = philox4x32_10_ks(make_uint4(site0 + uint32_t(l) * dsite, step_lo, step_hi, blk), keys);
     wav[l][0] = w.x;
     wav[l][1] = w.z;
-    ang[l][0] = fmaf((float)((int)w.y >> 9), kAngleScale, kAngleOffset);
-    ang[l][1] = fmaf((float)((int)w.w >> 9), kAngleScale, kAngleOffset);
+    ang[l][0] = fmaf((float)(int)w.y, kAngleScale, kAngleOffset);
+    ang[l][1] = fmaf((float)(int)w.w, kAngleScale, kAngleOffset);
   }
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     T x, kf;
 #pragma unroll
     for (int l = 0; l < L; ++l) {
+      // ix = bits(y) - bits(sqrt(1/2)) - 24 * 2^23: its top bits give k - 24 directly (an
+      // arithmetic shift; the range [-0x0BB504F3, 0x004AFB0C] cannot overflow) and its low 23
+      // bits the mantissa of x.
       const uint32_t y = (wav[l][p] >> 8) | 1u;
-      const uint32_t ix = __float_as_uint((float)y) - 0x3F3504F3u;
+      const uint32_t ix = __float_as_uint((float)y) - (0x3F3504F3u + (24u << 23));
       set_lane(x, l, __uint_as_float((ix & 0x007FFFFFu) + 0x3F3504F3u));
-      set_lane(kf, l, (float)(((int)ix >> 23) - 24));
+      set_lane(kf, l, (float)((int)ix >> 23));
     }
     const T t = vsub(x, splat<T>(1.0f));
     const T d = vadd(x, splat<T>(1.0f));
@@ -123,17 +127,15 @@ __device__ __forceinline__ void normals4_scaled(uint32_t site0, uint32_t step_lo
     P = vfma(P, s2, splat<T>(-4.0f / 3.0f));
     P = vfma(P, s2, splat<T>(-4.0f));
     const T a = vfma(kf, splat<T>(-1.38629436f), vmul(sx, P));  // -2 ln u_a (kf = k - 24)
-    T rad, c, sn;
+    const T rad = sqrt_fast_lanes(vmul(a, rho));  // sqrt(rho) sqrt(-2 ln u_a)
+    T c, sn;
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-      const float al = lane(a, l);
-      set_lane(rad, l, al * rsqrtf(al));
       float sl, cl;
       __sincosf(ang[l][p], &sl, &cl);
       set_lane(sn, l, sl);
       set_lane(c, l, cl);
     }
-    rad = vmul(rad, scale);
     z[2 * p] = vmul(rad, c);
     z[2 * p + 1] = vmul(rad, sn);
   }
