@@ -840,12 +840,17 @@ int batch_params(flbm_batch *b) {
     flbm_ctx *c = b->members[size_t(b->order[size_t(i)])];
     const StepArgs &a = c->args;
     BatchLattice &L = b->args->lats[i];
-    L.f = c->f;
+    L.f256 = uint32_t((static_cast<char *>(c->f) - static_cast<char *>(b->pool)) / 256);
     L.plane = uint32_t(c->N);
     L.nx = a.nx;
     L.ny = a.ny;
     L.nz = a.nz;
-    L.D = c->D;
+    uint32_t m = 0;
+    int p_hp = 0, p_ny = 0;
+    batch_magic(uint32_t((a.nx + 1) / 2), &L.m_hp, &p_hp);
+    batch_magic(uint32_t(a.ny), &m, &p_ny);
+    L.m_ny = m;
+    L.dpp = uint32_t(c->D) | (uint32_t(p_hp) << 8) | (uint32_t(p_ny) << 16);
     L.rho0 = a.rho0;
     L.key0 = a.key0;
     L.key1 = a.key1;
@@ -912,6 +917,7 @@ int batch_shape(flbm_batch *b) {
 // cooperative launch; the per-step form makes n plain launches and a counter update.
 int batch_enqueue(flbm_batch *b, int64_t n) {
   b->args->rates = b->d_rates;
+  b->args->pool = static_cast<char *>(b->pool);
   b->args->nlat = int(b->members.size());
   b->args->ntiles = b->ntiles;
   b->args->tile_slots = b->threads;

@@ -63,13 +63,18 @@ __device__ __forceinline__ uint32_t pair_slots(const BatchLattice &L) {
   return (uint32_t)((L.nx + 1) >> 1) * (uint32_t)L.ny * (uint32_t)L.nz;
 }
 
-// Row coordinates of pair slot `slot` (32-bit arithmetic: every site index is < 2^32)
-// and the site index of its first site: 2 slot when nx is even, 2 slot - r otherwise.
+__device__ __forceinline__ uint32_t udiv_magic(uint32_t x, uint32_t m, int p) {
+  return (uint32_t)(((unsigned long long)x * m) >> p);
+}
+
+// Row coordinates of pair slot `slot` (32-bit arithmetic: every site index is < 2^32, so
+// slots and rows are < 2^31) and the site index of its first site: 2 slot when nx is even,
+// 2 slot - r otherwise. The divisions use the lattice's multiply-shift constants.
 __device__ __forceinline__ uint32_t slot_xyz(const BatchLattice &L, uint32_t slot, int &x0, int &y, int &z) {
   const uint32_t hp = (uint32_t)((L.nx + 1) >> 1);
-  const uint32_t r = slot / hp;
+  const uint32_t r = udiv_magic(slot, L.m_hp, L.p_hp());
   x0 = 2 * (int)(slot - r * hp);
-  const uint32_t q = r / (uint32_t)L.ny;
+  const uint32_t q = udiv_magic(r, L.m_ny, L.p_ny());
   y = (int)(r - q * (uint32_t)L.ny);
   z = (int)q;
   return 2u * slot - ((L.nx & 1) ? r : 0u);
@@ -168,21 +173,25 @@ __device__ __forceinline__ void store_odd_pair(float *__restrict__ f, long long 
 // accesses through OddPair. Either way the neighbour addresses are recomputed at the
 // store rather than kept live across the collision (register pressure).
 template <int D, int PARITY, bool SHEAR, bool EVEN, bool ROLLED = true>
-__device__ __forceinline__ void batch_sites(const BatchLattice &L, const float *rates, uint32_t slot,
+__device__ __forceinline__ void batch_sites(const BatchLattice &L, char *pool, const float *rates, uint32_t slot,
                                             uint32_t step_lo, uint32_t step_hi) {
-  float *__restrict__ f = static_cast<float *>(L.f);
+  float *__restrict__ f = reinterpret_cast<float *>(pool + 256ull * L.f256);
   const long long plane = L.plane;
   float2 F[3][3][3];
-  uint32_t s0;
+  uint32_t s0, dsite = 1u;
   {
     int x0, y, z;
     s0 = slot_xyz(L, slot, x0, y, z);
-    if (EVEN)
-      load_logical2<D, float, PARITY>(f, plane, addr2(x0, y, z, L.nx, L.ny, L.nz), F);
-    else
+    if (EVEN) {  // the single-lattice pairing: odd steps take sites x0 + 1 and x0 + 2
+      const Addr2 ad = addr2(x0, y, z, L.nx, L.ny, L.nz);
+      load_pairs<D, float, PARITY>(f, plane, ad, F);
+      s0 = pair_site0<PARITY>(ad);
+      dsite = pair_dsite<PARITY>(ad);
+    } else {
       load_odd_pair<D, PARITY>(f, plane, odd_pair(x0, y, z, L.nx, L.ny, L.nz), F);
+    }
   }
-  collide_lattice<D, SHEAR, ROLLED>(F, L, rates, s0, 1u, step_lo, step_hi);
+  collide_lattice<D, SHEAR, ROLLED>(F, L, rates, s0, dsite, step_lo, step_hi);
   // The empty asm hides the slot's provenance so that the compiler cannot merge the
   // store's address computation with the load's (and keep 18 registers live).
   uint32_t sl = slot;
@@ -190,27 +199,28 @@ __device__ __forceinline__ void batch_sites(const BatchLattice &L, const float *
   int x0, y, z;
   slot_xyz(L, sl, x0, y, z);
   if (EVEN)
-    store_streamed2<D, float, PARITY>(f, plane, addr2(x0, y, z, L.nx, L.ny, L.nz), F);
+    store_pairs<D, float, PARITY>(f, plane, addr2(x0, y, z, L.nx, L.ny, L.nz), F);
   else
     store_odd_pair<D, PARITY>(f, plane, odd_pair(x0, y, z, L.nx, L.ny, L.nz), x0 + 1 < L.nx, F);
 }
 
 // Pair slot first + threadIdx.x of tile [first, end) of lattice L.
 template <int PARITY, bool SHEAR>
-__device__ __forceinline__ void batch_tile(const BatchLattice &L, const float *rates, uint32_t first, uint32_t end,
+__device__ __forceinline__ void batch_tile(const BatchLattice &L, char *pool, const float *rates, uint32_t first,
+                                           uint32_t end,
                                            uint32_t step_lo, uint32_t step_hi) {
   const uint32_t slot = first + threadIdx.x;
   if (slot >= end) return;
-  if (L.D == 3) {
+  if (L.D() == 3) {
     if (L.nx % 2 == 0)
-      batch_sites<3, PARITY, SHEAR, true>(L, rates, slot, step_lo, step_hi);
+      batch_sites<3, PARITY, SHEAR, true>(L, pool, rates, slot, step_lo, step_hi);
     else
-      batch_sites<3, PARITY, SHEAR, false>(L, rates, slot, step_lo, step_hi);
+      batch_sites<3, PARITY, SHEAR, false>(L, pool, rates, slot, step_lo, step_hi);
   } else {
     if (L.nx % 2 == 0)
-      batch_sites<2, PARITY, SHEAR, true>(L, rates, slot, step_lo, step_hi);
+      batch_sites<2, PARITY, SHEAR, true>(L, pool, rates, slot, step_lo, step_hi);
     else
-      batch_sites<2, PARITY, SHEAR, false>(L, rates, slot, step_lo, step_hi);
+      batch_sites<2, PARITY, SHEAR, false>(L, pool, rates, slot, step_lo, step_hi);
   }
 }
 
@@ -268,9 +278,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) batch_kernel(const BatchA
     const unsigned long long step = (unsigned long long)(step0 + s);
     const uint32_t lo = (uint32_t)step, hi = (uint32_t)(step >> 32);
     if (step & 1)
-      batch_tile<1, SHEAR>(L, a.rates + 54 * lat, first, end, lo, hi);
+      batch_tile<1, SHEAR>(L, a.pool, a.rates + 54 * lat, first, end, lo, hi);
     else
-      batch_tile<0, SHEAR>(L, a.rates + 54 * lat, first, end, lo, hi);
+      batch_tile<0, SHEAR>(L, a.pool, a.rates + 54 * lat, first, end, lo, hi);
     __syncthreads();  // every thread's writes of this tile are issued
     if (threadIdx.x == 0) {
       __threadfence();  // release
@@ -309,10 +319,11 @@ __global__ void __launch_bounds__(MINB >= 5 ? 128 : kBatchMaxThreads, MINB)
   if (slot >= end) return;
   const unsigned long long step = (unsigned long long)(*a.step_counter + k);
   const float *rates = a.rates + 54 * lat;
+  char *pool = a.pool;
   if (L.nx % 2 == 0)
-    batch_sites<D, PARITY, SHEAR, true, ROLLED>(L, rates, slot, (uint32_t)step, (uint32_t)(step >> 32));
+    batch_sites<D, PARITY, SHEAR, true, ROLLED>(L, pool, rates, slot, (uint32_t)step, (uint32_t)(step >> 32));
   else
-    batch_sites<D, PARITY, SHEAR, false, ROLLED>(L, rates, slot, (uint32_t)step, (uint32_t)(step >> 32));
+    batch_sites<D, PARITY, SHEAR, false, ROLLED>(L, pool, rates, slot, (uint32_t)step, (uint32_t)(step >> 32));
 }
 
 // Advances the shared step counter after the n step launches of one call.

@@ -41,16 +41,31 @@ constexpr int kBatchMaxLattices = 512;  // bound of the by-value lattice table b
 constexpr uint32_t kBatchWaitPolls = 1u << 22;  // polls of about a microsecond each
 
 struct BatchLattice {  // one lattice of a batch (FP32 storage); lives in the kernel arguments
-  void *f;
+  uint32_t f256;   // populations at pool + 256 f256 bytes (the batch's allocation)
   uint32_t plane;  // nx * ny * nz (< 2^32)
-  int nx, ny, nz, D;
+  int nx, ny, nz;
+  uint32_t dpp;    // D | p_hp << 8 | p_ny << 16 (lattice dimension and the shifts below)
   float rho0;
   uint32_t key0, key1;                  // noise key (seed)
   float sqrt_kbt, om_shear, phc_shear;  // rates in the paper's structure (ShearRates)
   int tile0;                            // index of the lattice's first tile
+  // Division by the row's pair-slot count and by ny as a multiply-high and a shift:
+  // q = (x * m) >> p with p = 31 + ceil(log2 d), m = ceil(2^p / d), exact for x < 2^31.
+  uint32_t m_hp, m_ny;
+  __host__ __device__ int D() const { return (int)(dpp & 0xFFu); }
+  __host__ __device__ int p_hp() const { return (int)((dpp >> 8) & 0xFFu); }
+  __host__ __device__ int p_ny() const { return (int)((dpp >> 16) & 0xFFu); }
 };
+// (m, p) of the division by d >= 1 described at BatchLattice.
+inline void batch_magic(uint32_t d, uint32_t *m, int *p) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  *p = 31 + l;
+  *m = (uint32_t)(((1ull << *p) + d - 1) / d);
+}
 struct BatchArgs {
   const float *rates;        // general rates: om[27] then phc[27] per lattice (device)
+  char *pool;                // the allocation holding every lattice's populations
   int nlat, ntiles, nsteps;  // lattices, tiles (all lattices), steps of this launch
   int tile_slots;            // pair slots (two x-adjacent sites) per tile = threads per block
   long long *step_counter;   // device: completed steps of every lattice
@@ -61,6 +76,7 @@ struct BatchArgs {
   uint32_t wait_polls;       // bound of each wait, in polls
   BatchLattice lats[kBatchMaxLattices];
 };
+static_assert(sizeof(BatchArgs) <= 32764, "batch kernel arguments exceed the parameter space");
 cudaError_t batch_max_blocks(bool shear, int threads, int *blocks_per_sm);
 cudaError_t launch_batch(bool shear, const BatchArgs &a, int grid, int threads, cudaStream_t s);
 // The lattices of one type: table entries [lat_lo, lat_hi) owning tiles
