@@ -79,6 +79,11 @@ def _load():
                                ctypes.c_uint64, ctypes.c_int64, dp, ctypes.c_int]
     lib.oracle_run.restype = ctypes.c_int64
     lib.oracle_stats.argtypes = [ctypes.c_int, i64p, dp, dp]
+    lib.oracle_collide_site_model.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, dp, dp, dp]
+    lib.oracle_collide_site_model.restype = ctypes.c_int
+    lib.oracle_run_model.argtypes = [ctypes.c_int, ctypes.c_int, i64p, dp, ctypes.c_double, ctypes.c_uint64,
+                                     ctypes.c_uint64, ctypes.c_int64, dp, ctypes.c_int]
+    lib.oracle_run_model.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -173,15 +178,21 @@ def site_eta(lat, seed, step, site):
     return eta
 
 
-def collide_site(lat, f, lam, kBT, eta):
-    """Return (f_star[Q], k_pre[Q]) for one site with given normals eta[Q]."""
+CM = 0   # collision models: central moments (the paper's scheme)
+RAW = 1  # raw moments (T = M); with a uniform rate, fluctuating BGK
+
+
+def collide_site(lat, f, lam, kBT, eta, model=CM):
+    """Return (f_star[Q], k_pre[Q]) for one site with given normals eta[Q]; k_pre are the
+    pre-collision moments of the model's basis (central for CM, raw for RAW)."""
     q = _Q[lat]
     f = _f64(f, q)
     lam = _f64(lam, q)
     eta = _f64(eta, q)
     fs = np.zeros(q)
     k = np.zeros(q)
-    rc = _load().oracle_collide_site(lat, _dp(f), _dp(lam), float(kBT), _dp(eta), _dp(fs), _dp(k))
+    rc = _load().oracle_collide_site_model(lat, int(model), _dp(f), _dp(lam), float(kBT), _dp(eta), _dp(fs),
+                                           _dp(k))
     if rc != 0:
         raise FloatingPointError("singular collision matrix")
     return fs, k
@@ -198,7 +209,7 @@ def init_uniform(lat, dims, rho0, u0=(0.0, 0.0, 0.0), amp=0.0, perturb_seed=0):
     return f
 
 
-def run(lat, dims, lam, kBT, seed, f, step0=0, nsteps=1, threads=0):
+def run(lat, dims, lam, kBT, seed, f, step0=0, nsteps=1, threads=0, model=CM):
     """Advance a copy of f[Q, nz, ny, nx] by nsteps steps; returns the new state."""
     d = _dims(lat, dims)
     q = _Q[lat]
@@ -206,8 +217,8 @@ def run(lat, dims, lam, kBT, seed, f, step0=0, nsteps=1, threads=0):
     if g.size != q * int(np.prod(d)):
         raise ValueError("population array has the wrong size")
     lam = _f64(lam, q)
-    bad = _load().oracle_run(lat, d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(lam),
-                             float(kBT), int(seed), int(step0), int(nsteps), _dp(g), int(threads))
+    bad = _load().oracle_run_model(lat, int(model), d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(lam),
+                                   float(kBT), int(seed), int(step0), int(nsteps), _dp(g), int(threads))
     if bad:
         raise FloatingPointError(f"{bad} singular collision matrices")
     return g.reshape(q, d[2], d[1], d[0])

@@ -440,8 +440,14 @@ void site_eta(int lat, uint64_t seed, uint64_t step, uint32_t site, double *eta)
 // One site's collision (Eq. cm_collision with Eq. phi_general). eta holds the
 // normals of the noisy modes (I~_v = 1 for v > D: Sec. II-B lists I~ =
 // diag[0,0,0,1,...,1] for D2Q9 and Sec. II-C lists I~_{0-3} = 0, I~_{4-26} = 1).
+// model 0: the central-moment scheme, k = T(u) f with k^eq = (rho, 0, ..., 0).
+// model 1: its raw-moment counterpart, T = M (N = I, Sec. II-C: "Setting T = M reduces
+// the scheme to its raw-moments counterpart"): k = M f, k^eq = M f^eq(rho, u), the same
+// relaxation, noise amplitudes and normals; with a uniform rate Lambda = omega I it is the
+// fluctuating BGK scheme of Sec. II-A (relaxation omega (f^eq - f), noise zeta_i of
+// Eq. Xi_pop in the rest-frame basis).
 bool collide_site(int lat, const double *f, const double *lambda, double kBT, const double *eta,
-                  double *fstar, double *k_out) {
+                  double *fstar, double *k_out, int model = 0) {
   const Lattice &L = lattice(lat);
   const int Q = L.Q;
   double rho = 0.0, j[3] = {0, 0, 0};
@@ -451,15 +457,24 @@ bool collide_site(int lat, const double *f, const double *lambda, double kBT, co
   }
   const double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
   std::vector<double> T;
-  build_T(lat, u, T);
-  std::vector<double> k(Q, 0.0), kstar(Q, 0.0);
+  const double zero[3] = {0.0, 0.0, 0.0};
+  build_T(lat, model == 1 ? zero : u, T);  // raw moments: the unshifted basis M = T(0)
+  std::vector<double> k(Q, 0.0), kstar(Q, 0.0), keqv(Q, 0.0);
   for (int v = 0; v < Q; ++v)
     for (int i = 0; i < Q; ++i) k[v] += T[v * Q + i] * f[i];
   if (k_out)
     for (int v = 0; v < Q; ++v) k_out[v] = k[v];
+  if (model == 1) {
+    double fe[27];
+    feq(lat, rho, u, fe);
+    for (int v = 0; v < Q; ++v)
+      for (int i = 0; i < Q; ++i) keqv[v] += T[v * Q + i] * fe[i];
+  } else {
+    keqv[0] = rho;
+  }
   for (int v = 0; v < Q; ++v) {
     const double lam = (v <= L.D) ? 1.0 : lambda[v];
-    const double keq = (v == 0) ? rho : 0.0;
+    const double keq = keqv[v];
     const double noisy = (v > L.D) ? 1.0 : 0.0;
     double phi = 0.0;
     if (noisy != 0.0 && kBT != 0.0) phi = std::sqrt(rho * kBT * lam * (2.0 - lam) * bnorm(lat, v) / CS2);
@@ -530,6 +545,12 @@ int oracle_collide_site(int lat, const double *f, const double *lambda, double k
   return collide_site(lat, f, lambda, kBT, eta, fstar, k_out) ? 0 : 1;
 }
 
+// As oracle_collide_site for collision model `model` (0 central moments, 1 raw moments).
+int oracle_collide_site_model(int lat, int model, const double *f, const double *lambda, double kBT,
+                              const double *eta, double *fstar, double *k_out) {
+  return collide_site(lat, f, lambda, kBT, eta, fstar, k_out, model) ? 0 : 1;
+}
+
 // Initial state: rho(x) = rho0 (1 + amp (2U - 1)), U = uniform of word 0 of the
 // tag-1 Philox block (counter (site, 0, 0, 2^16)) under key perturb_seed;
 // f = feq(rho(x), u0).
@@ -556,8 +577,8 @@ void oracle_init_uniform(int lat, const int64_t *dims, double rho0, const double
 // Each step: collide every site, push-stream into a second lattice, swap.
 // threads <= 0 uses the OpenMP default. Returns the number of sites whose
 // collision matrix was singular (0 normally).
-int64_t oracle_run(int lat, const int64_t *dims, const double *lambda, double kBT, uint64_t seed,
-                   uint64_t step0, int64_t nsteps, double *f, int threads) {
+int64_t oracle_run_model(int lat, int model, const int64_t *dims, const double *lambda, double kBT,
+                         uint64_t seed, uint64_t step0, int64_t nsteps, double *f, int threads) {
   const Lattice &L = lattice(lat);
   const int Q = L.Q;
   const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
@@ -578,7 +599,7 @@ int64_t oracle_run(int lat, const int64_t *dims, const double *lambda, double kB
       for (int i = 0; i < Q; ++i) fl[i] = f[i * N + site];
       for (int v = 0; v < Q; ++v) eta[v] = 0.0;
       if (kBT != 0.0) site_eta(lat, seed, step, uint32_t(site), eta);
-      if (!collide_site(lat, fl, lambda, kBT, eta, fs, nullptr)) ++bad;
+      if (!collide_site(lat, fl, lambda, kBT, eta, fs, nullptr, model)) ++bad;
       for (int i = 0; i < Q; ++i) {
         const int64_t xd = ((x + L.c[i][0]) % nx + nx) % nx;
         const int64_t yd = ((y + L.c[i][1]) % ny + ny) % ny;
@@ -589,6 +610,12 @@ int64_t oracle_run(int lat, const int64_t *dims, const double *lambda, double kB
     std::memcpy(f, g.data(), sizeof(double) * g.size());
   }
   return bad;
+}
+
+// The central-moment scheme (model 0).
+int64_t oracle_run(int lat, const int64_t *dims, const double *lambda, double kBT, uint64_t seed,
+                   uint64_t step0, int64_t nsteps, double *f, int threads) {
+  return oracle_run_model(lat, 0, dims, lambda, kBT, seed, step0, nsteps, f, threads);
 }
 
 // Statistics of the state f (pre-collision): out layout (doubles)
