@@ -234,6 +234,23 @@ int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storage, int pari
  */
 int flbm_set_step_variant(flbm_ctx *ctx, int variant);
 int flbm_get_step_variant(const flbm_ctx *ctx);
+
+/*
+ * Collision model of a context (default FLBM_COLLISION_CM, the paper's scheme).
+ * FLBM_COLLISION_RAW is its raw-moment counterpart, the comparison scheme of the paper:
+ * T = M and N = I ("Setting T = M reduces the scheme to its raw-moments counterpart",
+ * Sec. II-C), i.e. the same basis, rates, amplitudes phi_v (Eq. phi_general) and normals,
+ * applied to the raw moments M f with the equilibrium raw moments M f^eq(rho, u). With
+ * every non-conserved rate equal to omega it is the fluctuating BGK step of Sec. II-A:
+ * f* = f + omega (f^eq - f) + zeta with zeta_i = w_i sum_v b_v^-1 M_vi phi_v eta_v
+ * (Eq. Xi_pop). Available for FLBM_D2Q9 and FLBM_D3Q27 (FLBM_EINVAL otherwise), not for the
+ * lattices of a batch (FLBM_ESTATE); step variants 1 and 2 only (others run as 2, odd nx as
+ * 1). Statistics still report the central moments of the orthogonal basis. The model is
+ * saved in checkpoints. Takes effect at the next flbm_step.
+ */
+enum flbm_collision { FLBM_COLLISION_CM = 0, FLBM_COLLISION_RAW = 1 };
+int flbm_set_collision(flbm_ctx *ctx, int model);
+int flbm_get_collision(const flbm_ctx *ctx); /* -1 for a NULL ctx */
 int flbm_autotune(flbm_ctx *ctx, int trial_steps, int *chosen);
 
 /* Wait for the context's stream. FLBM_ECUDA carries any asynchronous device error. */

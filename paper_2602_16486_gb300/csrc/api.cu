@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -61,6 +62,7 @@ struct flbm_ctx {
   int64_t gdims[3] = {1, 1, 1};  // the whole lattice
   int64_t z_begin = 0, z_count = 0;
   bool in_domain = false;  // a slab owned by a flbm_domain (stepped by it)
+  int model = FLBM_COLLISION_CM;  // enum flbm_collision
 };
 
 namespace {
@@ -276,6 +278,8 @@ int enqueue_stats(flbm_ctx *c, double *acc_dev) {
 // is even, else one site per thread); the pipelined choice falls back where it does not
 // apply.
 int resolve_variant(const flbm_ctx *c) {
+  if (c->model == FLBM_COLLISION_RAW)  // raw-moment kernels: one site or two per thread
+    return c->dims[0] % 2 != 0 || c->variant == kStepOneSite ? int(kStepOneSite) : int(kStepPair);
   const bool pipe = pipe_applicable(c->D, c->storage, int(c->dims[0]));
   int v = c->variant;
   if (v == kStepAuto) v = kStepPair;
@@ -301,13 +305,14 @@ int check_status(flbm_ctx *c) {
 
 struct CkptHeader {
   char magic[8];
-  int32_t version, lattice, storage, q;
+  int32_t version, lattice, storage, q;  // version 2 adds `model` (version 1: central moments)
   int64_t dims[3];
   int64_t step;
   uint64_t seed;
   double kBT, rho0;
   double lambda[27];
   uint64_t payload_bytes;
+  int32_t model, pad;
 };
 const char kMagic[8] = {'F', 'L', 'B', 'M', 'C', 'K', 'P', '1'};
 
@@ -442,8 +447,11 @@ int flbm_step(flbm_ctx *c, int64_t n) {
   for (int64_t s = 0; s < n; ++s) {
     c->args.step_lo = uint32_t(uint64_t(c->step));
     c->args.step_hi = uint32_t(uint64_t(c->step) >> 32);
-    FLBM_CUDA(launch_step(c->lattice, c->storage, resolve_variant(c), int(c->step & 1), noise, c->shear,
-                          c->args, c->stream));
+    if (c->model == FLBM_COLLISION_RAW)
+      FLBM_CUDA(launch_step_raw(c->D, c->storage, resolve_variant(c), int(c->step & 1), noise, c->args, c->stream));
+    else
+      FLBM_CUDA(launch_step(c->lattice, c->storage, resolve_variant(c), int(c->step & 1), noise, c->shear,
+                            c->args, c->stream));
     ++c->step;
   }
   return FLBM_OK;
@@ -607,7 +615,8 @@ int flbm_save(flbm_ctx *c, void *host, size_t bytes) {
   DeviceGuard g(c->device);
   CkptHeader h{};
   std::memcpy(h.magic, kMagic, 8);
-  h.version = 1;
+  h.version = 2;
+  h.model = c->model;
   h.lattice = c->lattice;
   h.storage = c->storage;
   h.q = c->Q;
@@ -628,27 +637,36 @@ int flbm_save(flbm_ctx *c, void *host, size_t bytes) {
 int flbm_load(flbm_ctx *c, const void *host, size_t bytes) {
   if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
   if (!host) return fail(FLBM_EINVAL, "host is NULL");
-  if (bytes < sizeof(CkptHeader)) return fail(FLBM_EINVAL, "blob too small for a checkpoint header");
-  CkptHeader h;
-  std::memcpy(&h, host, sizeof(h));
-  if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) return fail(FLBM_EINVAL, "not a checkpoint blob");
+  // Version 1 headers end before `model`.
+  constexpr size_t kHeaderV1 = offsetof(CkptHeader, model);
+  if (bytes < kHeaderV1) return fail(FLBM_EINVAL, "blob too small for a checkpoint header");
+  CkptHeader h{};
+  std::memcpy(&h, host, kHeaderV1);
+  const size_t hbytes = h.version == 1 ? kHeaderV1 : sizeof(CkptHeader);
+  if (h.version == 2 && bytes >= sizeof(CkptHeader)) std::memcpy(&h, host, sizeof(h));
+  if (std::memcmp(h.magic, kMagic, 8) != 0 || (h.version != 1 && h.version != 2))
+    return fail(FLBM_EINVAL, "not a checkpoint blob");
+  if (h.version == 1) h.model = FLBM_COLLISION_CM;
+  if (h.model != FLBM_COLLISION_CM && (h.model != FLBM_COLLISION_RAW || c->owner))
+    return fail(FLBM_EINVAL, "checkpoint collision model %d is not available for this context", h.model);
   if (h.lattice != c->lattice || h.storage != c->storage || h.dims[0] != c->dims[0] ||
       h.dims[1] != c->dims[1] || h.dims[2] != c->dims[2] || h.payload_bytes != c->f_bytes)
     return fail(FLBM_EINVAL, "checkpoint lattice, dims or storage differ from the context");
-  if (bytes < sizeof(h) + h.payload_bytes) return fail(FLBM_EINVAL, "checkpoint blob truncated");
+  if (bytes < hbytes + h.payload_bytes) return fail(FLBM_EINVAL, "checkpoint blob truncated");
   const int st = check_params(h.lattice, h.lambda, h.kBT, h.rho0);
   if (st != FLBM_OK) return st;
   if (c->owner && h.step != c->step)
     return fail(FLBM_ESTATE, "checkpoint of step %lld, the batch is at step %lld", (long long)h.step,
                 (long long)c->step);
   DeviceGuard g(c->device);
-  FLBM_CUDA(cudaMemcpyAsync(c->f, static_cast<const char *>(host) + sizeof(h), c->f_bytes,
+  FLBM_CUDA(cudaMemcpyAsync(c->f, static_cast<const char *>(host) + hbytes, c->f_bytes,
                             cudaMemcpyHostToDevice, c->stream));
   FLBM_CUDA(cudaStreamSynchronize(c->stream));
   c->step = h.step;
   c->seed = h.seed;
   c->kBT = h.kBT;
   c->rho0 = h.rho0;
+  c->model = h.model;
   for (int v = 0; v < c->Q; ++v) c->lambda[v] = (v <= c->D) ? 1.0 : h.lambda[v];
   fill_args(c);
   c->params_changed = true;
@@ -665,6 +683,19 @@ int flbm_set_step_variant(flbm_ctx *c, int variant) {
 }
 
 int flbm_get_step_variant(const flbm_ctx *c) { return c ? resolve_variant(c) : -1; }
+
+int flbm_set_collision(flbm_ctx *c, int model) {
+  if (!c) return fail(FLBM_EINVAL, "ctx is NULL");
+  if (model != FLBM_COLLISION_CM && model != FLBM_COLLISION_RAW)
+    return fail(FLBM_EINVAL, "collision model %d is not FLBM_COLLISION_CM (0) or FLBM_COLLISION_RAW (1)", model);
+  if (c->owner) return fail(FLBM_ESTATE, "the lattices of a batch use the central-moment collision");
+  if (model == FLBM_COLLISION_RAW && c->lattice != FLBM_D2Q9 && c->lattice != FLBM_D3Q27)
+    return fail(FLBM_EINVAL, "the raw-moment collision is available for FLBM_D2Q9 and FLBM_D3Q27 only");
+  c->model = model;
+  return FLBM_OK;
+}
+
+int flbm_get_collision(const flbm_ctx *c) { return c ? c->model : -1; }
 
 int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
   if (!c) return fail(FLBM_EINVAL, "ctx is NULL");

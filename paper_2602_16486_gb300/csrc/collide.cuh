@@ -91,6 +91,86 @@ __device__ __forceinline__ void add_noise_block(T (&F)[3][3][3], const R &rates,
 // are rotated back before the inverse transform. With SHEAR and ISO every non-conserved
 // mode but 4-9 relaxes at rate 1; modes 4-9 are formed directly from the raw second
 // moments: k_aa = P_aa - rho u_a^2, k_ab = P_ab - rho u_a u_b.
+// The raw-moment counterpart of the scheme (T = M, N = I; Sec. II-C notes that this
+// reduces the collision to raw moments, and with a uniform rate to the fluctuating BGK
+// operator of Sec. II-A): the moments of the tile stay raw, the equilibrium raw moments
+// of mode (a, b, c) are rho m_a(u_x) m_b(u_y) m_c(u_z) with m = (1, u, u^2) (the raw moments
+// of the product equilibrium in the 1-D basis {1, c, c^2 - cs^2}), the non-conserved modes
+// relax as k*_v = k^eq_v + (1 - L_v)(k_v - k^eq_v) + phi_v eta_v with the same amplitudes and
+// normals, and only the raw inverse follows (halved convention, as below).
+template <int D, bool NOISE, typename T, typename R, typename K>
+__device__ __forceinline__ void collide_raw(T (&F)[3][3][3], float rho0, const R &rates, uint32_t site0,
+                                            uint32_t step_lo, uint32_t step_hi, const K &keys, uint32_t dsite) {
+  T drho, rho, ux, uy, uz;
+  site_macros<D>(F, rho0, drho, rho, ux, uy, uz);  // raw moments of the deviations
+  const T one = splat<T>(1.0f);
+  const T mx[3] = {one, ux, vmul(ux, ux)}, my[3] = {one, uy, vmul(uy, uy)}, mz[3] = {one, uz, vmul(uz, uz)};
+  if (D == 3) {
+#pragma unroll
+    for (int v = 4; v < 27; ++v) {
+      const int t = d3q27_mode_tensor(v);
+      T &k = F[t / 9][(t / 3) % 3][t % 3];
+      const T keq = vmul(vmul(rho, mx[t % 3]), vmul(my[(t / 3) % 3], mz[t / 9]));
+      k = vfma(splat<T>(rates.om(v)), vsub(k, keq), vmul(splat<T>(tile_scale<3>(v)), keq));
+    }
+    if (NOISE) {
+#pragma unroll
+      for (int blk = 0; blk < 6; ++blk) {
+        T z[4];
+        normals4_scaled<T>(site0, step_lo, step_hi, (uint32_t)blk, keys, rho, z, dsite);
+        switch (blk) {
+          case 0: add_noise_block<0>(F, rates, z); break;
+          case 1: add_noise_block<1>(F, rates, z); break;
+          case 2: add_noise_block<2>(F, rates, z); break;
+          case 3: add_noise_block<3>(F, rates, z); break;
+          case 4: add_noise_block<4>(F, rates, z); break;
+          default: add_noise_block<5>(F, rates, z); break;
+        }
+      }
+    }
+    const T h = splat<T>(0.5f);  // momentum slots in the halved convention
+    F[0][0][1] = vmul(h, F[0][0][1]);
+    F[0][1][0] = vmul(h, F[0][1][0]);
+    F[1][0][0] = vmul(h, F[1][0][0]);
+  } else {
+    const T rxx = F[1][0][2], ryy = F[1][2][0];
+    const T exx = vmul(rho, mx[2]), eyy = vmul(rho, my[2]);
+    T k[9], keq[9];
+    k[3] = vadd(rxx, ryy);
+    keq[3] = vadd(exx, eyy);
+    k[4] = vsub(rxx, ryy);
+    keq[4] = vsub(exx, eyy);
+    k[5] = F[1][1][1];
+    keq[5] = vmul(vmul(rho, ux), uy);
+    k[6] = F[1][1][2];
+    keq[6] = vmul(exx, uy);
+    k[7] = F[1][2][1];
+    keq[7] = vmul(eyy, ux);
+    k[8] = F[1][2][2];
+    keq[8] = vmul(exx, my[2]);
+#pragma unroll
+    for (int v = 3; v < 9; ++v)
+      k[v] = vfma(splat<T>(rates.om(v)), vsub(k[v], keq[v]), vmul(splat<T>(tile_scale<2>(v)), keq[v]));
+    if (NOISE) {
+      T z0[4], z1[4];
+      normals4_scaled<T>(site0, step_lo, step_hi, 0u, keys, rho, z0, dsite);
+      normals4_scaled<T>(site0, step_lo, step_hi, 1u, keys, rho, z1, dsite);
+#pragma unroll
+      for (int v = 3; v < 9; ++v) k[v] = vfma(splat<T>(rates.phc(v)), v < 7 ? z0[v - 3] : z1[v - 7], k[v]);
+    }
+    const T h = splat<T>(0.5f);
+    F[1][0][2] = vmul(h, vadd(k[3], k[4]));
+    F[1][2][0] = vmul(h, vsub(k[3], k[4]));
+    F[1][1][1] = k[5];
+    F[1][1][2] = k[6];
+    F[1][2][1] = k[7];
+    F[1][2][2] = k[8];
+    F[1][0][1] = vmul(h, F[1][0][1]);
+    F[1][1][0] = vmul(h, F[1][1][0]);
+  }
+  tile_raw_inv_h<D>(F);  // entry (0,0,0) still holds rho - rho0
+}
+
 template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false, bool ISO = false, typename R,
           typename K>
 __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const R &rates, uint32_t site0,
@@ -239,13 +319,18 @@ __device__ __forceinline__ void collide_rates(T (&F)[3][3][3], float rho0, const
 
 // The collision with per-mode arrays om_v, phc_v (kernel arguments).
 // dsite: site index of a pair's lane y minus that of lane x (1, or 1 - nx across a row's end).
-template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false, bool ISO = false>
+// RAW: the raw-moment counterpart (collide_raw).
+template <int D, bool NOISE, typename T, bool ROLLED = false, bool SHEAR = false, bool ISO = false,
+          bool RAW = false>
 __device__ __forceinline__ void collide_tile(T (&F)[3][3][3], float rho0, const float *om,
                                              const float *phc, uint32_t site0, uint32_t step_lo,
                                              uint32_t step_hi, const uint32_t *ks0,
                                              const uint32_t *ks1, uint32_t dsite = 1) {
-  collide_rates<D, NOISE, T, ROLLED, SHEAR, ISO>(F, rho0, ArrayRates{om, phc}, site0, step_lo, step_hi,
-                                            KeyTable{ks0, ks1}, dsite);
+  if constexpr (RAW)
+    collide_raw<D, NOISE, T>(F, rho0, ArrayRates{om, phc}, site0, step_lo, step_hi, KeyTable{ks0, ks1}, dsite);
+  else
+    collide_rates<D, NOISE, T, ROLLED, SHEAR, ISO>(F, rho0, ArrayRates{om, phc}, site0, step_lo, step_hi,
+                                                   KeyTable{ks0, ks1}, dsite);
 }
 
 }  // namespace flbm

@@ -129,6 +129,9 @@ cudaError_t launch_step_d3q19(int storage, int variant, int parity, bool noise, 
                               cudaStream_t s);
 cudaError_t launch_step_pipelined(int D, int storage, int parity, bool noise, bool shear,
                                   const StepArgs &a, cudaStream_t s);
+// The raw-moment collision (step_raw.cu): D 2 or 3, variants 1 (one site) and 2 (pairs).
+cudaError_t launch_step_raw(int D, int storage, int variant, int parity, bool noise, const StepArgs &a,
+                            cudaStream_t s);
 // Statistics of the sites [site0, site0 + nsites) of the array (the whole box: 0, plane).
 cudaError_t launch_stats(int D, int storage, bool iso, int parity, const void *f, long long plane, int nx,
                          int ny, int nz, float rho0, double *acc, cudaStream_t s, long long site0,

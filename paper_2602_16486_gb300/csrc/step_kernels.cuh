@@ -13,7 +13,7 @@
 namespace flbm {
 namespace {
 
-template <int D, typename S, int PARITY, bool NOISE, bool SHEAR, bool ISO>
+template <int D, typename S, int PARITY, bool NOISE, bool SHEAR, bool ISO, bool RAW = false>
 __global__ void __launch_bounds__(kStepBlock) step_kernel(const StepArgs a) {
   const int x = blockIdx.x * kStepBlock + threadIdx.x;
   if (x >= a.nx) return;
@@ -24,12 +24,12 @@ __global__ void __launch_bounds__(kStepBlock) step_kernel(const StepArgs a) {
   float F[3][3][3];
   load_logical<D, S, PARITY>(f, a.plane, nb, F);
   const uint32_t site = (uint32_t)(x + (long long)a.nx * (y + (long long)a.ny * z)) + a.site_base;
-  collide_tile<D, NOISE, float, false, SHEAR, ISO>(F, a.rho0, a.om_t, a.phc_t, site, a.step_lo, a.step_hi, a.ks0,
-                                                   a.ks1);
+  collide_tile<D, NOISE, float, false, SHEAR, ISO, RAW>(F, a.rho0, a.om_t, a.phc_t, site, a.step_lo, a.step_hi,
+                                                        a.ks0, a.ks1);
   store_streamed<D, S, PARITY>(f, a.plane, nb, F);
 }
 
-template <int D, typename S, int PARITY, bool NOISE, bool ROLLED, bool SHEAR, int MINB, bool ISO>
+template <int D, typename S, int PARITY, bool NOISE, bool ROLLED, bool SHEAR, int MINB, bool ISO, bool RAW = false>
 __global__ void __launch_bounds__(kStepBlock, MINB) step2_kernel(const StepArgs a) {
   const int x0 = 2 * (blockIdx.x * kStepBlock + threadIdx.x);
   if (x0 >= a.nx) return;
@@ -38,8 +38,9 @@ __global__ void __launch_bounds__(kStepBlock, MINB) step2_kernel(const StepArgs 
 
   float2 F[3][3][3];
   load_pairs<D, S, PARITY>(f, a.plane, ad, F);
-  collide_tile<D, NOISE, float2, ROLLED, SHEAR, ISO>(F, a.rho0, a.om_t, a.phc_t, pair_site0<PARITY>(ad) + a.site_base,
-                                                     a.step_lo, a.step_hi, a.ks0, a.ks1, pair_dsite<PARITY>(ad));
+  collide_tile<D, NOISE, float2, ROLLED, SHEAR, ISO, RAW>(F, a.rho0, a.om_t, a.phc_t,
+                                                          pair_site0<PARITY>(ad) + a.site_base, a.step_lo,
+                                                          a.step_hi, a.ks0, a.ks1, pair_dsite<PARITY>(ad));
   store_pairs<D, S, PARITY>(f, a.plane, ad, F);
 }
 
@@ -96,6 +97,19 @@ cudaError_t launch_typed(int variant, int parity, bool noise, bool shear, const 
                  : launch_kernel<D, S, 1, true, false, ISO>(variant, a, s);
   return shear ? launch_kernel<D, S, 1, false, true, ISO>(variant, a, s)
                : launch_kernel<D, S, 1, false, false, ISO>(variant, a, s);
+}
+
+// The raw-moment counterpart (collide_raw): one site per thread or two (nx even).
+template <int D, typename S, int PARITY, bool NOISE>
+cudaError_t launch_raw_kernel(int variant, const StepArgs &a, cudaStream_t s) {
+  const dim3 block(kStepBlock);
+  if (variant == kStepOneSite)
+    step_kernel<D, S, PARITY, NOISE, false, false, true>
+        <<<dim3((a.nx + kStepBlock - 1) / kStepBlock, a.ny, a.nz_grid), block, 0, s>>>(a);
+  else
+    step2_kernel<D, S, PARITY, NOISE, false, false, 4, false, true>
+        <<<dim3((a.nx / 2 + kStepBlock - 1) / kStepBlock, a.ny, a.nz_grid), block, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace

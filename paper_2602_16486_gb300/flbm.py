@@ -106,6 +106,8 @@ def _load():
         "flbm_sync": (ctypes.c_int, [vp]),
         "flbm_set_step_variant": (ctypes.c_int, [vp, ctypes.c_int]),
         "flbm_get_step_variant": (ctypes.c_int, [vp]),
+        "flbm_set_collision": (ctypes.c_int, [vp, ctypes.c_int]),
+        "flbm_get_collision": (ctypes.c_int, [vp]),
         "flbm_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "flbm_stats_noalloc": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_double, vp, vp, ctypes.POINTER(flbm_stats_t)]),
@@ -321,6 +323,18 @@ def flbm_set_step_variant(ctx, variant):
 
 def flbm_get_step_variant(ctx):
     return int(_lib.flbm_get_step_variant(ctx))
+
+
+FLBM_COLLISION_CM = 0
+FLBM_COLLISION_RAW = 1
+
+
+def flbm_set_collision(ctx, model):
+    _check(_lib.flbm_set_collision(ctx, int(model)))
+
+
+def flbm_get_collision(ctx):
+    return int(_lib.flbm_get_collision(ctx))
 
 
 def flbm_autotune(ctx, trial_steps=10):
@@ -575,6 +589,15 @@ class Lattice:
 
     def autotune(self, trial_steps=10):
         return flbm_autotune(self.ctx, trial_steps)
+
+    @property
+    def collision(self):
+        """FLBM_COLLISION_CM (the paper's scheme) or FLBM_COLLISION_RAW (raw moments)."""
+        return flbm_get_collision(self.ctx)
+
+    @collision.setter
+    def collision(self, model):
+        flbm_set_collision(self.ctx, model)
 
     @property
     def variant(self):
