@@ -4,17 +4,18 @@
 // Every recorded sum is an entry of G = sum_x c(x) c(x)^T over the per-site column
 //   c = [1, rho - rho0, j_x, j_y, j_z, u_x, u_y, u_z, k_{D+1} .. k_{Q-1}, 0 ...]
 // (NC = 32 entries for D3Q27 and D3Q19, 16 for D2Q9). G is a dense contraction over the
-// sites, so it runs on the tensor cores: warp-level mma.sync m16n8k8 with TF32 inputs and
-// FP32 accumulation, each input split into x_hi = tf32(x) (rounded to nearest) and
-// x_lo = x - x_hi (exact in FP32; the tensor core reads its leading TF32 bits), and every
-// product formed as hi*hi + hi*lo + lo*hi (about 2^-21 relative accuracy per product;
-// x_lo takes either sign, so dropping its trailing bits adds no bias). A block of
-// kStatsBlock threads works on tiles of 2 kStatsBlock sites, each thread on two. Each
-// warp owns 32 rows of the shared-memory tile (one row per site): its lanes stage the
-// split columns of their first site there (row 32 w + lane), the warp accumulates the
-// upper block-triangle of G over those 32 rows in FP32 fragments, and the same follows
-// for the second site. Warps therefore only synchronise among their own lanes
-// (__syncwarp), never with the block.
+// sites, so it runs on the tensor cores: warp-level mma.sync m16n8k16 with BF16 inputs and
+// FP32 accumulation, the K dimension running over sites. Each input is split into
+// x_hi = bf16(x) and x_lo = bf16(x - x_hi) (both rounded to nearest; x - x_hi is exact in
+// FP32), and every product is formed as hi*hi + hi*lo + lo*hi + lo*lo: what is left out is
+// the rounding of x_lo, about 2^-16 of x with either sign, so the products carry no bias
+// and about 2^-15 relative error each. BF16 keeps FP32's exponent range, so no column needs
+// scaling. A block of kStatsBlock threads works on tiles of 2 kStatsBlock sites, each
+// thread on two: its pair packs into one bf16x2 word per column (the pair of K indices an
+// MMA fragment register holds). Each warp owns 32 rows of the shared-memory tile (one row
+// per thread, i.e. per site pair): its lanes stage the split columns there, and the warp
+// accumulates the upper block-triangle of G over those 64 sites in FP32 fragments. Warps
+// therefore only synchronise among their own lanes (__syncwarp), never with the block.
 // The fragments go to the block's FP64 sums in shared memory every kFlushTiles tiles;
 // at the end the block adds its sums to the output record with one FP64 atomic per
 // entry. Output record: the upper triangle of G in FP64, row-major, then the number of
@@ -42,9 +43,9 @@ struct StatsPlan {
 namespace gram {
 
 constexpr int kTileSites = 2 * kStatsBlock;  // two sites per thread
-constexpr int kRows = kStatsBlock;           // staged rows: one site of every thread
+constexpr int kRows = kStatsBlock;           // staged rows: the site pair of every thread
 constexpr int kFlushTiles = 16;  // FP32 sums over at most 16 x 64 sites per fragment entry
-                                  // (a tile gives every warp two passes of 32 sites)
+                                  // (a tile gives every warp 64 sites)
 
 template <int D>
 __host__ __device__ constexpr int tile_mt(int i) {
@@ -55,7 +56,7 @@ __host__ __device__ constexpr int tile_nt(int i) {
   return D != 2 ? (i < 4 ? i : i - 2) : i;
 }
 
-// A shared-memory row holds the 32 words of one site in eight 16-byte chunks: chunk g
+// A shared-memory row holds the 32 words of one site pair in eight 16-byte chunks: chunk g
 // carries the columns g, g + 8, g + 16, g + 24, which are the words a lane with
 // g = lane / 4 needs for its A fragments (rows g and g + 8 of both 16-row tiles), so a
 // fragment row comes in with one 16-byte load (8-byte for D2Q9, whose 16 columns use
@@ -65,27 +66,26 @@ __host__ __device__ constexpr int tile_nt(int i) {
 // loading fragments (rows s0 + t or s0 + t + 4, chunks g).
 __device__ __forceinline__ int chunk_pos(int g, int r) { return g ^ ((r & 3) << 1) ^ ((r >> 2) & 1); }
 
-// Round to TF32 (nearest, ties away). x_hi must be rounded, not truncated: a truncated
-// x_hi leaves x_lo with the sign of x, and the dropped bits of x_lo would then shrink
-// every product by about 2^-21 on average.
-__device__ __forceinline__ uint32_t to_tf32(float x) {
+// bf16x2 of (a, b): a in the low half (the lower K index), b in the high half; rounded to
+// nearest.
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
   return r;
 }
 
-// D (16x8, FP32) += A (16x8, TF32, row-major) * B (8x8, TF32, column-major). Not
+// D (16x8, FP32) += A (16x16, BF16, row-major) * B (16x8, BF16, column-major). Not
 // volatile: the compiler may interleave independent accumulations.
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
   asm(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
       "{%0, %1, %2, %3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// The block's shared memory: TF32 high and low parts of the tile's columns, then the FP64
-// sums of every warp's fragments.
+// The block's shared memory: BF16 high and low parts of the tile's columns (bf16x2 words,
+// one per site pair and column), then the FP64 sums of every warp's fragments.
 template <int D>
 struct Smem {
   uint32_t *hi, *lo;
@@ -167,8 +167,8 @@ __device__ __forceinline__ void moment_columns(const float2 (&F)[3][3][3], float
 // The row of this thread: 32 w + lane (w: its warp).
 __device__ __forceinline__ int own_row() { return threadIdx.x; }
 
-// Split column of site L (0: lane x, 1: lane y of the pair) of this thread into its row.
-template <int L, int D, int NC>
+// Split columns of this thread's site pair (lane x: lower K index) into its row.
+template <int D, int NC>
 __device__ __forceinline__ void stage_columns(const Smem<D> &s, const float2 (&col)[NC]) {
   constexpr int LD = StatsPlan<D>::LD, P = NC / 8;  // words used per chunk
   const int r = own_row();
@@ -177,9 +177,10 @@ __device__ __forceinline__ void stage_columns(const Smem<D> &s, const float2 (&c
     uint32_t h[4], e[4];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-      const float x = L == 0 ? col[g + 8 * p].x : col[g + 8 * p].y;
-      h[p] = to_tf32(x);
-      e[p] = __float_as_uint(x - __uint_as_float(h[p]));
+      const float2 x = col[g + 8 * p];
+      h[p] = pack_bf16x2(x.x, x.y);
+      const float hx = __uint_as_float(h[p] << 16), hy = __uint_as_float(h[p] & 0xFFFF0000u);
+      e[p] = pack_bf16x2(x.x - hx, x.y - hy);  // exact differences, rounded to BF16
     }
     const int w = r * LD + 4 * chunk_pos(g, r);
     if (P == 4) {
@@ -209,11 +210,12 @@ struct Warp {
     off_b = 4 * chunk_pos(g, t + 4);
   }
 
-  // This warp's 32 rows of the staged tile, 8 sites per MMA step (the K dimension); the
-  // caller has made its lanes' staging visible (__syncwarp). Rows s0 + t and s0 + t + 4
-  // (s0 a multiple of 8) keep their chunk positions at every step, so the steps only
-  // move the row base. A fragments: a0, a1 = columns m0 + g, m0 + g + 8 of site t;
-  // a2, a3 = the same columns of site t + 4 (m0 = 0, 16).
+  // This warp's 32 rows (64 sites) of the staged tile, 8 rows = 16 sites per MMA step (the
+  // K dimension); the caller has made its lanes' staging visible (__syncwarp). Rows s0 + t
+  // and s0 + t + 4 (s0 a multiple of 8) keep their chunk positions at every step, so the
+  // steps only move the row base. A fragments: a0, a1 = columns m0 + g, m0 + g + 8 of the
+  // site pair of row t (K indices 2t, 2t + 1); a2, a3 = the same columns of row t + 4
+  // (K indices 2t + 8, 2t + 9), m0 = 0, 16.
   __device__ __forceinline__ void tile(const Smem<D> &s) {
     const int warp = threadIdx.x >> 5, t = threadIdx.x & 3;
     constexpr int LD = P::LD;
@@ -244,14 +246,16 @@ struct Warp {
         bl[nt][0] = al[mt][h];
         bl[nt][1] = al[mt][h + 2];
       }
-      // hi*hi, then hi*lo, then lo*hi over all tiles: consecutive MMAs go to different
+      // hi*hi, hi*lo, lo*hi, then lo*lo over all tiles: consecutive MMAs go to different
       // accumulators, so none waits for the one before it.
 #pragma unroll
-      for (int i = 0; i < P::NTILE; ++i) mma_tf32(d[i], ah[tile_mt<D>(i)], bh[tile_nt<D>(i)]);
+      for (int i = 0; i < P::NTILE; ++i) mma_bf16(d[i], ah[tile_mt<D>(i)], bh[tile_nt<D>(i)]);
 #pragma unroll
-      for (int i = 0; i < P::NTILE; ++i) mma_tf32(d[i], ah[tile_mt<D>(i)], bl[tile_nt<D>(i)]);
+      for (int i = 0; i < P::NTILE; ++i) mma_bf16(d[i], ah[tile_mt<D>(i)], bl[tile_nt<D>(i)]);
 #pragma unroll
-      for (int i = 0; i < P::NTILE; ++i) mma_tf32(d[i], al[tile_mt<D>(i)], bh[tile_nt<D>(i)]);
+      for (int i = 0; i < P::NTILE; ++i) mma_bf16(d[i], al[tile_mt<D>(i)], bh[tile_nt<D>(i)]);
+#pragma unroll
+      for (int i = 0; i < P::NTILE; ++i) mma_bf16(d[i], al[tile_mt<D>(i)], bl[tile_nt<D>(i)]);
     }
   }
 

@@ -4,12 +4,12 @@
 // "Structural properties"), plus mass and momentum for the conservation checks.
 //
 // Every one of these sums is an entry of the Gram matrix G of the per-site columns
-// (gram.cuh: layout, TF32 three-pass tensor-core accumulation, output record; k_0 = rho
+// (gram.cuh: layout, BF16 four-pass tensor-core accumulation, output record; k_0 = rho
 // and the central moments k_1..k_D, which vanish identically, are rebuilt or set to zero
 // by the host, api.cu). Persistent blocks of kStatsBlock threads walk tiles of
 // 2 kStatsBlock sites: each thread computes the columns of two sites with the packed
-// FP32x2 algebra of the step (cm.cuh) and stages them, one site at a time, in its warp's
-// rows; each warp then accumulates the Gram fragments of its rows.
+// FP32x2 algebra of the step (cm.cuh) and stages them in its warp's rows (one row per
+// pair, BF16 hi/lo words); each warp then accumulates the Gram fragments of its rows.
 #include <cuda_runtime.h>
 
 #include <map>
@@ -161,13 +161,9 @@ __global__ void __launch_bounds__(kStatsBlock, PAIRROW ? 4 : 3) stats_kernel(con
         pair_columns<D, S, PARITY, PAIRROW, ISO>(f, plane, nx, ny, nz, rho0, base + 2 * threadIdx.x, N, col,
                                                  nonfinite);
       }
-      // First the lane-x sites, then the lane-y sites, each in the warp's own rows; the
-      // rows are consumed (second __syncwarp) before they are overwritten.
-      gram::stage_columns<0, D>(sm, col);
-      __syncwarp();
-      gw.tile(sm);
-      __syncwarp();
-      gram::stage_columns<1, D>(sm, col);
+      // The thread's site pair in the warp's own rows; the rows are consumed (second
+      // __syncwarp) before the next tile overwrites them.
+      gram::stage_columns<D>(sm, col);
       __syncwarp();
       gw.tile(sm);
       __syncwarp();

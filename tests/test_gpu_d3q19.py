@@ -4,6 +4,8 @@ Tolerance as everywhere: max |f_gpu - f_oracle| / (w_i rho0) <= 1e-5."""
 import numpy as np
 import pytest
 
+from _gram_tol import uu_tol
+
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
@@ -82,7 +84,8 @@ def test_d3q19_stats_match_oracle(fl, oracle_mod):
     ref = oracle_mod.stats(Q19, dims, f)
     assert st["q"] == 19
     assert st["mass"] == pytest.approx(ref["mass"], rel=1e-7)
-    np.testing.assert_allclose(st["uu"], ref["uu"], rtol=1e-5, atol=1e-11)
+    n = int(np.prod(dims))  # near-zero entries: the reduction's own error (tests/_gram_tol.py)
+    assert np.all(np.abs(np.asarray(st["uu"]) - ref["uu"]) <= 1e-5 * np.abs(ref["uu"]) + uu_tol(ref["uu"], n))
     scale = np.sqrt(np.abs(np.diag(ref["k_cov"])))
     np.testing.assert_allclose(st["k_mean"][:19], ref["k_mean"], atol=1e-5 * scale.max() + 1e-9)
     np.testing.assert_allclose(st["k_cov"], ref["k_cov"], rtol=1e-4, atol=1e-5 * np.outer(scale, scale).max())
