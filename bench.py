@@ -604,8 +604,8 @@ def run_profile_workload(args):
     stats: a D3Q27 box of --dims, two steps, two statistics reductions; d3q19: a D3Q19 box
     of --dims with the paper's rates (shear 1.6), four steps of --variant (default 2);
     batch: the 256-lattice ensemble, three steps of the per-step five-blocks form;
-    step: the headline physics on a D3Q27 box of --dims in --storage, four steps of
-    --variant (default 5)."""
+    step: the headline physics on a D3Q27 box of --dims in --storage (D2Q9 when the box has
+    nz = 1), four steps of --variant (default 5)."""
     import torch
 
     import paper_2602_16486_gb300 as fl
@@ -619,9 +619,11 @@ def run_profile_workload(args):
             lat.stats()
             lat.stats()
     elif args.profile == "step":
-        with fl.Lattice(fl.FLBM_D3Q27, dims, lam_d3q27(), KBT, 1.0, SEED, args.storage) as lat:
+        lattice = fl.FLBM_D2Q9 if dims[2] == 1 else fl.FLBM_D3Q27
+        lam = _lam_for(lattice)
+        with fl.Lattice(lattice, dims, lam, KBT, 1.0, SEED, args.storage) as lat:
             lat.variant = args.variant or 5
-            lat.init_uniform(U0, AMP, SEED)
+            lat.init_uniform(U0 if lattice else U0[:2] + (0.0,), AMP, SEED)
             lat.step(4)
             lat.sync()
     elif args.profile == "d3q19":

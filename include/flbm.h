@@ -223,14 +223,17 @@ int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storage, int pari
  * shared memory with bulk asynchronous copies (needs nx even, nx <= 512 and a
  * population row a multiple of 16 bytes; else it falls back to 2), 5 and 6 = 2 and 3
  * compiled for more resident blocks per SM to hide latency: five for the 3-D lattices
- * (at most 102 registers), ten for D2Q9 (at most 51). Variants 2-6 fall back to 1 when
+ * (at most 102 registers), eight for D2Q9 (at most 64). Variants 2-6 fall back to 1 when
  * nx is odd. The environment variable FLBM_STEP_VARIANT, read by flbm_create, sets the
  * initial choice.
  * flbm_autotune times every applicable variant over trial_steps steps on a copy of the
  * current state (restored afterwards: populations and step count are unchanged), keeps
  * the fastest for this context and caches the choice per (GPU model, lattice, storage,
- * nx parity, size class, noise on/off) for the process. Needs one extra copy of the
- * populations in device memory while it runs. Synchronises.
+ * nx parity, size class, noise on/off, rate structure) for the process; when the
+ * environment variable FLBM_AUTOTUNE_CACHE names a file, choices are also read from it
+ * (at the first flbm_autotune call of the process) and appended to it (one
+ * "key<TAB>variant" line per choice), so later processes skip the trials. Needs one extra
+ * copy of the populations in device memory while it runs. Synchronises.
  */
 int flbm_set_step_variant(flbm_ctx *ctx, int variant);
 int flbm_get_step_variant(const flbm_ctx *ctx);

@@ -709,12 +709,29 @@ int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
   int size_class = 0;
   for (long long n = c->N; n > 1; n >>= 1) ++size_class;
   char key[320];
-  std::snprintf(key, sizeof(key), "%s|%d|%d|%d|%d|%d|%d", prop.name, c->lattice, c->storage,
-                int(c->dims[0] % 2), size_class, c->kBT > 0.0 ? 1 : 0, c->shear ? 1 : 0);
+  std::snprintf(key, sizeof(key), "%s|%d|%d|%d|%d|%d|%d|%d", prop.name, c->lattice, c->storage,
+                int(c->dims[0] % 2), size_class, c->kBT > 0.0 ? 1 : 0, c->shear ? 1 : 0, c->model);
   static std::mutex mu;
   static std::map<std::string, int> cache;
+  static bool file_read = false;
+  const char *cache_file = std::getenv("FLBM_AUTOTUNE_CACHE");
   {
     std::lock_guard<std::mutex> lock(mu);
+    if (cache_file && *cache_file && !file_read) {
+      // One "key<TAB>variant" line per choice; malformed lines are skipped.
+      file_read = true;
+      if (FILE *fh = std::fopen(cache_file, "r")) {
+        char line[512];
+        while (std::fgets(line, sizeof(line), fh)) {
+          char *tab = std::strchr(line, '\t');
+          if (!tab) continue;
+          *tab = '\0';
+          const int v = std::atoi(tab + 1);
+          if (v >= kStepOneSite && v <= kStepVariantMax) cache[line] = v;
+        }
+        std::fclose(fh);
+      }
+    }
     auto it = cache.find(key);
     if (it != cache.end()) {
       c->variant = it->second;
@@ -784,6 +801,11 @@ int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
   {
     std::lock_guard<std::mutex> lock(mu);
     cache[key] = best_v;
+    if (cache_file && *cache_file)
+      if (FILE *fh = std::fopen(cache_file, "a")) {
+        std::fprintf(fh, "%s\t%d\n", key, best_v);
+        std::fclose(fh);
+      }
   }
   if (chosen) *chosen = best_v;
   return FLBM_OK;

@@ -58,8 +58,9 @@ cudaError_t launch_kernel(int variant, const StepArgs &a, cudaStream_t s) {
   if (variant != kStepOneSite) {
     // Register caps: 128 (four blocks of 128 threads per SM) or, for variants 5 and 6,
     // 102 for D3Q27 (five blocks: more warps to hide latency, at the risk of spills) and
-    // 51 for the lighter D2Q9 update (ten blocks).
-    constexpr int kOcc = D == 3 ? 5 : 10;
+    // 64 for the lighter D2Q9 update (eight blocks; ten, at 51 registers, left the even
+    // step waiting on its loads: 0.214 against 0.183 ms at 4096^2).
+    constexpr int kOcc = D == 3 ? 5 : 8;
     const dim3 grid((a.nx / 2 + kStepBlock - 1) / kStepBlock, a.ny, a.nz_grid);
     const bool occ = variant == kStepPairOcc || variant == kStepPairRolledOcc;
     const bool rolled = !ISO && (variant == kStepPairRolled || variant == kStepPairRolledOcc);

@@ -229,7 +229,7 @@ def test_storage_precision_against_oracle_replica(fl, kbt, oracle_mod):
     kk_ref = np.mean([x["kk"] for x in ser], axis=0)
     noisy = np.arange(4, 27)
     # Bounds: FP32 storage rounds each value to 2^-24 of itself and follows the oracle's
-    # trajectory (1e-5); 16-bit storage rounds each deviation to 2^-9 (BF16) or 2^-12
+    # trajectory (1e-5); 16-bit storage rounds each deviation to 2^-8 (BF16) or 2^-11
     # (FP16) of itself every step, an unbiased perturbation whose effect on second
     # moments is of order 2^-18 (1e-3 leaves a wide margin; measured about 1e-5).
     for storage, tol in ((0, 1e-5), (1, 1e-3), (2, 1e-3)):
