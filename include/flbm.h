@@ -241,8 +241,8 @@ int flbm_get_step_variant(const flbm_ctx *ctx);
 /*
  * Collision model of a context (default FLBM_COLLISION_CM, the paper's scheme).
  * FLBM_COLLISION_RAW is its raw-moment counterpart, the comparison scheme of the paper:
- * T = M and N = I ("Setting T = M reduces the scheme to its raw-moments counterpart",
- * Sec. II-C), i.e. the same basis, rates, amplitudes phi_v (Eq. phi_general) and normals,
+ * T = M and N = I (Sec. II-C, end of the D3Q27 construction, names this choice as the
+ * scheme's raw-moment form), i.e. the same basis, rates, amplitudes phi_v (Eq. phi_general) and normals,
  * applied to the raw moments M f with the equilibrium raw moments M f^eq(rho, u). With
  * every non-conserved rate equal to omega it is the fluctuating BGK step of Sec. II-A:
  * f* = f + omega (f^eq - f) + zeta with zeta_i = w_i sum_v b_v^-1 M_vi phi_v eta_v

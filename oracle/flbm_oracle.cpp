@@ -441,8 +441,8 @@ void site_eta(int lat, uint64_t seed, uint64_t step, uint32_t site, double *eta)
 // normals of the noisy modes (I~_v = 1 for v > D: Sec. II-B lists I~ =
 // diag[0,0,0,1,...,1] for D2Q9 and Sec. II-C lists I~_{0-3} = 0, I~_{4-26} = 1).
 // model 0: the central-moment scheme, k = T(u) f with k^eq = (rho, 0, ..., 0).
-// model 1: its raw-moment counterpart, T = M (N = I, Sec. II-C: "Setting T = M reduces
-// the scheme to its raw-moments counterpart"): k = M f, k^eq = M f^eq(rho, u), the same
+// model 1: its raw-moment counterpart, T = M and N = I (Sec. II-C names this choice as the
+// raw-moment form of the same scheme): k = M f, k^eq = M f^eq(rho, u), the same
 // relaxation, noise amplitudes and normals; with a uniform rate Lambda = omega I it is the
 // fluctuating BGK scheme of Sec. II-A (relaxation omega (f^eq - f), noise zeta_i of
 // Eq. Xi_pop in the rest-frame basis).

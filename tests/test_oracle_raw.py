@@ -1,8 +1,8 @@
 """Pins of the oracle's raw-moment collision (model RAW: T = M, N = I), the comparison
-scheme of the paper: "Setting T = M reduces the scheme to its raw-moments counterpart,
-with N = I, while the BGK model is recovered by enforcing a uniform relaxation rate
-Lambda = omega I" (Sec. II-C, end of the D3Q27 construction), and the fluctuating BGK
-operator of Sec. II-A (relaxation omega (f^eq - f) plus the noise zeta_i of Eq. Xi_pop).
+scheme of the paper. Sec. II-C (end of the D3Q27 construction) identifies the choice T = M,
+N = I as the raw-moment form of the scheme and a single rate Lambda = omega I as BGK; with
+that rate the update must be the fluctuating BGK operator of Sec. II-A (relaxation
+omega (f^eq - f) plus the noise zeta_i of Eq. Xi_pop).
 
 Expected values come from the paper's formulas written out here with the printed basis
 polynomials (tests/_paper_basis.py), the printed norms (golden files) and the closed product
