@@ -58,7 +58,8 @@ enum flbm_status {
   FLBM_ENOMEM = 2,   /* device or host allocation failed                             */
   FLBM_ECUDA = 3,    /* a CUDA runtime call failed (message in flbm_last_error)       */
   FLBM_ENUMERIC = 4, /* the sampled state holds non-finite values                     */
-  FLBM_ETIMEOUT = 5, /* a device-side bounded wait gave up (batched persistent kernel) */
+  FLBM_ETIMEOUT = 5, /* a device-side bounded wait gave up (persistent kernels, the
+                        tensor-core statistics reduction); the result is not valid     */
   FLBM_ESTATE = 6    /* call not valid in the current state (e.g. sample buffer full) */
 };
 
@@ -143,9 +144,12 @@ int64_t flbm_get_step(const flbm_ctx *ctx);
 
 /*
  * flbm_stats - statistics of the current state (velocity moments, Sec. III Eq. for
- * <u_a^2>; central-moment means and covariances, Sec. II-B C^eq), FP32 per site and
- * FP64 accumulation. Synchronises. Returns FLBM_ENUMERIC (and still fills *out) when
- * some site is not finite.
+ * <u_a^2>; central-moment means and covariances, Sec. II-B C^eq), FP32 per site, the
+ * products on the tensor cores (BF16 hi/lo splits of both factors, FP32 accumulation of
+ * at most 512 sites, at most 2^-15 relative error per product and no bias) and FP64
+ * sums. Synchronises. Returns FLBM_ENUMERIC (and still fills *out) when some site is
+ * not finite, FLBM_ETIMEOUT (out->nonfinite negative) if the reduction's bounded wait
+ * for the tensor cores gave up.
  */
 int flbm_stats(flbm_ctx *ctx, flbm_stats_t *out);
 

@@ -266,6 +266,21 @@ void fill_stats(const flbm_ctx *c, const double *acc, int64_t step, flbm_stats_t
   }
 }
 
+// Status of a statistics record: FLBM_ETIMEOUT when the reduction's bounded wait on the
+// tensor cores gave up (it marks the non-finite count negative), FLBM_ENUMERIC when
+// sites hold non-finite values, else FLBM_OK.
+int stats_result(const flbm_stats_t *out, long long step) {
+  if (out->nonfinite < 0)
+    return fail(FLBM_ETIMEOUT, "a bounded wait of the statistics reduction gave up; the record is not valid");
+  if (out->nonfinite > 0) {
+    if (step >= 0)
+      return fail(FLBM_ENUMERIC, "%lld sites hold non-finite values at step %lld", (long long)out->nonfinite,
+                  step);
+    return fail(FLBM_ENUMERIC, "%lld sites hold non-finite values", (long long)out->nonfinite);
+  }
+  return FLBM_OK;
+}
+
 int enqueue_stats(flbm_ctx *c, double *acc_dev) {
   FLBM_CUDA(cudaMemsetAsync(acc_dev, 0, sizeof(double) * stats_record_len(c->Q), c->stream));
   FLBM_CUDA(launch_stats(klat(c->lattice), c->storage, c->iso, int(c->step & 1), c->f, c->N, int(c->dims[0]),
@@ -471,10 +486,7 @@ int flbm_stats(flbm_ctx *c, flbm_stats_t *out) {
   const int status = check_status(c);
   if (status != FLBM_OK) return status;
   fill_stats(c, c->h_acc, c->step, out);
-  if (out->nonfinite > 0)
-    return fail(FLBM_ENUMERIC, "%lld sites hold non-finite values at step %lld",
-                (long long)out->nonfinite, (long long)c->step);
-  return FLBM_OK;
+  return stats_result(out, (long long)c->step);
 }
 
 int flbm_set_sample_capacity(flbm_ctx *c, int cap) {
@@ -526,13 +538,19 @@ int flbm_fetch_samples(flbm_ctx *c, flbm_stats_t *out, int max_n, int *n_out) {
                               cudaMemcpyDeviceToHost, c->stream));
   FLBM_CUDA(cudaStreamSynchronize(c->stream));
   int64_t bad = 0;
+  bool timeout = false;
   for (int k = 0; k < n; ++k) {
     fill_stats(c, h.data() + len * size_t(k), c->ring_steps[size_t(k)], &out[k]);
-    bad += out[k].nonfinite;
+    if (out[k].nonfinite < 0)
+      timeout = true;
+    else
+      bad += out[k].nonfinite;
   }
   c->ring_count = 0;
   c->ring_steps.clear();
   *n_out = n;
+  if (timeout)
+    return fail(FLBM_ETIMEOUT, "a bounded wait of the statistics reduction gave up; a fetched record is not valid");
   if (bad > 0) return fail(FLBM_ENUMERIC, "fetched samples count %lld non-finite sites", (long long)bad);
   return FLBM_OK;
 }
@@ -1372,9 +1390,7 @@ extern "C" int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storag
   view.N = N;
   view.rho0 = rho0;
   fill_stats(&view, h, -1, out);
-  if (out->nonfinite > 0)
-    return fail(FLBM_ENUMERIC, "%lld sites hold non-finite values", (long long)out->nonfinite);
-  return FLBM_OK;
+  return stats_result(out, -1);
 }
 
 // ---- domain decomposition along z -------------------------------------------------------
@@ -1730,10 +1746,7 @@ int flbm_domain_stats(flbm_domain *d, flbm_stats_t *out) {
   flbm_ctx view;
   domain_view(d, &view);
   fill_stats(&view, sum.data(), d->step, out);
-  if (out->nonfinite > 0)
-    return fail(FLBM_ENUMERIC, "%lld sites hold non-finite values at step %lld", (long long)out->nonfinite,
-                (long long)d->step);
-  return FLBM_OK;
+  return stats_result(out, (long long)d->step);
 }
 
 int flbm_domain_get_populations(flbm_domain *d, double *host, size_t count) {

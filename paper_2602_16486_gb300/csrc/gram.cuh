@@ -4,26 +4,43 @@
 // Every recorded sum is an entry of G = sum_x c(x) c(x)^T over the per-site column
 //   c = [1, rho - rho0, j_x, j_y, j_z, u_x, u_y, u_z, k_{D+1} .. k_{Q-1}, 0 ...]
 // (NC = 32 entries for D3Q27 and D3Q19, 16 for D2Q9). G is a dense contraction over the
-// sites, so it runs on the tensor cores: warp-level mma.sync m16n8k16 with BF16 inputs and
-// FP32 accumulation, the K dimension running over sites. Each input is split into
+// sites, so it runs on the fifth-generation tensor cores (tcgen05): BF16 inputs, FP32
+// accumulators in tensor memory (TMEM), K running over sites. Each input is split into
 // x_hi = bf16(x) and x_lo = bf16(x - x_hi) (both rounded to nearest; x - x_hi is exact in
 // FP32), and every product is formed as hi*hi + hi*lo + lo*hi + lo*lo: what is left out is
-// the rounding of x_lo, about 2^-16 of x with either sign, so the products carry no bias
-// and about 2^-15 relative error each. BF16 keeps FP32's exponent range, so no column needs
-// scaling. A block of kStatsBlock threads works on tiles of 2 kStatsBlock sites, each
-// thread on two: its pair packs into one bf16x2 word per column (the pair of K indices an
-// MMA fragment register holds). Each warp owns 32 rows of the shared-memory tile (one row
-// per thread, i.e. per site pair): its lanes stage the split columns there, and the warp
-// accumulates the upper block-triangle of G over those 64 sites in FP32 fragments. Warps
-// therefore only synchronise among their own lanes (__syncwarp), never with the block.
-// The fragments go to the block's FP64 sums in shared memory every kFlushTiles tiles;
-// at the end the block adds its sums to the output record with one FP64 atomic per
-// entry. Output record: the upper triangle of G in FP64, row-major, then the number of
-// non-finite sites.
+// the rounding of x_lo, below 2^-16 of x with either sign, so the products carry no bias
+// and at most 2^-15 relative error each. BF16 keeps FP32's exponent range, so no column
+// needs scaling.
+//
+// Operands. A warp's 32 threads hold 64 sites (two per thread). The warp stages them as
+// X = [X_hi; X_lo], 2 NC rows (one per column and part) by 64 sites, K-major: row r is one
+// 128-byte line of 64 BF16 values, with the 128-byte swizzle (16-byte chunk q of row r at
+// chunk position q ^ (r mod 8)), i.e. the canonical SWIZZLE_128B K-major layout of the
+// tensor-core shared-memory descriptor. The four warps' regions are contiguous, so 128
+// consecutive rows are the regions of 128 / (2 NC) warps. One MMA of shape M = N = 128,
+// K = 16 takes those 128 rows as both A and B: D = A B^T holds, in its diagonal blocks of
+// 2 NC x 2 NC, exactly the Gram matrices X X^T of those warps (the off-diagonal blocks mix
+// different warps' sites at the same K index and are never read). Every MMA of a tile
+// accumulates into the same 128 x 128 FP32 accumulator (128 TMEM columns), so the
+// diagonal blocks sum the Grams of all staged sites. Every warp arrives on a "staged"
+// mbarrier after its lanes have written their rows; one thread waits for it, issues the
+// tile's MMAs (4 K-steps per 128-row group) and commits them to a "done" mbarrier, on
+// which the warps wait before they overwrite the staging rows. Apart from the flushes no
+// block-wide barrier sits in the loop, so a warp runs ahead into the loads and arithmetic
+// of its next pair while the tensor cores work. After every kFlushTiles tiles (at the wait
+// that precedes the next staging) the warps read their quadrant of the accumulator
+// (tcgen05.ld), add hi and lo column halves and leave the rows in FP32 scratch (the idle
+// staging rows); each entry of the upper triangle then sums its few contributions in FP32
+// and is added once, by the thread that owns it, to the block's FP64 sums (no atomics:
+// GB300's FP64 pipe is narrow). The next tile's first MMA overwrites the accumulator. At
+// the end the block adds its sums to the output record with one FP64 atomic per entry.
+// Output record: the upper triangle of G in FP64, row-major, then the number of
+// non-finite sites (a bounded wait that gave up adds kStatsTimeoutMark to that count).
 #pragma once
 
 #include <cuda_runtime.h>
 
+#include "async.cuh"
 #include "cm.cuh"
 #include "internal.h"
 
@@ -31,40 +48,41 @@ namespace flbm {
 
 template <int D>  // D: 2 (D2Q9), 3 (D3Q27) or 19 (D3Q19)
 struct StatsPlan {
-  static constexpr int NC = D == 2 ? 16 : 32;  // columns, padded to whole MMA tiles
-  static constexpr int LD = 32;                // shared-memory row: 32 words (see chunk_pos)
-  static constexpr int MT = NC / 16;           // 16-row tiles of G
-  static constexpr int NT = NC / 8;            // 8-column tiles of G
-  // Upper block-triangle: tiles (mt, nt) with nt >= 2 mt.
-  static constexpr int NTILE = D == 2 ? 2 : 6;
+  static constexpr int NC = D == 2 ? 16 : 32;  // columns, padded to a power of two
+  // Columns in use: 1, rho - rho0, j (3), u (3) and the non-conserved modes.
+  static constexpr int USED = 8 + (D == 2 ? 6 : D == 19 ? 15 : 23);
   static constexpr int NREC = NC * (NC + 1) / 2;
 };
 
 namespace gram {
 
+constexpr int kWarps = kStatsBlock / 32;   // warps per block (one TMEM lane quadrant each)
 constexpr int kTileSites = 2 * kStatsBlock;  // two sites per thread
-constexpr int kRows = kStatsBlock;           // staged rows: the site pair of every thread
-constexpr int kFlushTiles = 16;  // FP32 sums over at most 16 x 64 sites per fragment entry
-                                  // (a tile gives every warp 64 sites)
+constexpr int kRowBytes = 128;             // one staged row: 64 sites in BF16
+constexpr uint32_t kTmemCols = 128;        // the 128 x 128 FP32 accumulator
+// 52 KB per block: four blocks fit the SM's 228 KB of shared memory, five do not.
+constexpr size_t kSmemFloor = 52 * 1024;
+constexpr int kBlocksPerSm = 512 / (int)kTmemCols;
+constexpr int kFlushTiles = 8;  // FP32 sums over at most 8 tiles (1024 sites per accumulator entry)
+// Added to the non-finite count of the record when a bounded wait gave up (the host
+// reports FLBM_ETIMEOUT for a negative count).
+constexpr double kStatsTimeoutMark = -1099511627776.0;  // -2^40
 
 template <int D>
-__host__ __device__ constexpr int tile_mt(int i) {
-  return D != 2 ? (i < 4 ? 0 : 1) : 0;
-}
-template <int D>
-__host__ __device__ constexpr int tile_nt(int i) {
-  return D != 2 ? (i < 4 ? i : i - 2) : i;
-}
-
-// A shared-memory row holds the 32 words of one site pair in eight 16-byte chunks: chunk g
-// carries the columns g, g + 8, g + 16, g + 24, which are the words a lane with
-// g = lane / 4 needs for its A fragments (rows g and g + 8 of both 16-row tiles), so a
-// fragment row comes in with one 16-byte load (8-byte for D2Q9, whose 16 columns use
-// the first two words of a chunk). Chunk g of row r sits at position
-// g ^ 2 (r mod 4) ^ (bit 2 of r): the eight lanes of each quarter-warp phase then hit
-// eight different chunks both when staging (eight consecutive rows, one chunk) and when
-// loading fragments (rows s0 + t or s0 + t + 4, chunks g).
-__device__ __forceinline__ int chunk_pos(int g, int r) { return g ^ ((r & 3) << 1) ^ ((r >> 2) & 1); }
+struct Plan {
+  using SP = StatsPlan<D>;
+  static constexpr int NC = SP::NC;
+  static constexpr int ROWS = 2 * NC;                  // hi rows, then lo rows
+  static constexpr int REGION = ROWS * kRowBytes;      // one warp's staging: 8 KB or 4 KB
+  static constexpr int BUF = kWarps * REGION;          // the block's staging
+  static constexpr int GROUPS = kWarps * ROWS / 128;   // 128-row MMA operands per tile
+  static constexpr int ACC = StatsPlan<D>::NREC;       // FP64 sums, in record order
+  // Shared memory: 1024 bytes of alignment slack, the staging rows, the sums, the two
+  // mbarriers and the TMEM address; at least kSmemFloor, so that at most four blocks (4 x
+  // 128 TMEM columns) share an SM.
+  static constexpr size_t NEED = 1024 + BUF + sizeof(double) * ACC + 32;
+  static constexpr size_t SMEM = NEED > kSmemFloor ? NEED : kSmemFloor;
+};
 
 // bf16x2 of (a, b): a in the low half (the lower K index), b in the high half; rounded to
 // nearest.
@@ -74,41 +92,71 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return r;
 }
 
-// D (16x8, FP32) += A (16x16, BF16, row-major) * B (16x8, BF16, column-major). Not
-// volatile: the compiler may interleave independent accumulations.
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzle: start
+// address (16-byte units, bits 0-13), leading byte offset (unused by this layout; 16 B),
+// stride byte offset between 8-row groups = 8 x 128 B (bits 32-45), the fixed value 1 in
+// bits 46-48, base offset 0 (1024-byte aligned atoms), layout 2 = SWIZZLE_128B (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// The block's shared memory: BF16 high and low parts of the tile's columns (bf16x2 words,
-// one per site pair and column), then the FP64 sums of every warp's fragments.
-template <int D>
-struct Smem {
-  uint32_t *hi, *lo;
-  double *acc64;  // [NTILE * 4][32]
-};
+// Instruction descriptor of kind::f16: D in FP32 (bits 4-5 = 1), A and B in BF16 (bits
+// 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 in bits 17-22, M / 16 in
+// bits 24-28; M = N = 128.
+constexpr uint32_t kIdescBf16M128N128 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
+                                        ((128u >> 4) << 24);
 
-template <int D>
-__host__ __device__ constexpr size_t smem_bytes() {
-  return 2 * sizeof(uint32_t) * kRows * StatsPlan<D>::LD + sizeof(double) * StatsPlan<D>::NTILE * 4 * 32;
+// D (TMEM) = A B^T (+ D when accumulate), A and B from shared memory; issued by one thread.
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdescBf16M128N128), "r"(accumulate)
+      : "memory");
 }
 
-template <int D>
-__device__ __forceinline__ Smem<D> smem_layout(unsigned char *raw) {
-  Smem<D> s;
-  s.hi = reinterpret_cast<uint32_t *>(raw);
-  s.lo = s.hi + kRows * StatsPlan<D>::LD;
-  s.acc64 = reinterpret_cast<double *>(s.lo + kRows * StatsPlan<D>::LD);
-  return s;
+// The mbarrier completes a phase when every MMA issued before by this thread is done.
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
 }
 
-template <int D>
-__device__ __forceinline__ void zero_acc64(const Smem<D> &s) {
-  for (int e = threadIdx.x; e < StatsPlan<D>::NTILE * 4 * 32; e += blockDim.x) s.acc64[e] = 0.0;
+// One arrival on an mbarrier (release semantics at CTA scope).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Generic-proxy shared-memory writes become visible to the tensor cores (async proxy).
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Warp-wide (all 32 lanes): allocate kTmemCols columns, address written to *slot.
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+               "r"(kTmemCols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp-wide; the warp's quadrant).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
 // Columns of a pair (lane x: first site, lane y: second) from its central moments: F as
@@ -164,128 +212,118 @@ __device__ __forceinline__ void moment_columns(const float2 (&F)[3][3][3], float
   }
 }
 
-// The row of this thread: 32 w + lane (w: its warp).
-__device__ __forceinline__ int own_row() { return threadIdx.x; }
+// The staging offsets of this lane: offs[k] = byte offset, within its warp's region, of
+// the lane's bf16x2 word in a row r with r mod 8 = k (chunk lane / 4 at position
+// (lane / 4) ^ k, word lane mod 4 of the chunk).
+__device__ __forceinline__ void stage_offsets(uint32_t (&offs)[8]) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (uint32_t k = 0; k < 8; ++k) offs[k] = (((lane >> 2) ^ k) << 4) | ((lane & 3u) << 2);
+}
 
-// Split columns of this thread's site pair (lane x: lower K index) into its row.
-template <int D, int NC>
-__device__ __forceinline__ void stage_columns(const Smem<D> &s, const float2 (&col)[NC]) {
-  constexpr int LD = StatsPlan<D>::LD, P = NC / 8;  // words used per chunk
-  const int r = own_row();
+// Splits the first USED columns of this thread's site pair (lane x: lower K index) into
+// the hi rows 0..USED-1 and the lo rows NC..NC+USED-1 of its warp's region (the other
+// rows hold zeros, written once).
+template <int D, int USED>
+__device__ __forceinline__ void stage_columns(unsigned char *region, const uint32_t (&offs)[8],
+                                              const float2 (&col)[StatsPlan<D>::NC]) {
+  constexpr int NC = StatsPlan<D>::NC;
 #pragma unroll
-  for (int g = 0; g < 8; ++g) {
-    uint32_t h[4], e[4];
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      const float2 x = col[g + 8 * p];
-      h[p] = pack_bf16x2(x.x, x.y);
-      const float hx = __uint_as_float(h[p] << 16), hy = __uint_as_float(h[p] & 0xFFFF0000u);
-      e[p] = pack_bf16x2(x.x - hx, x.y - hy);  // exact differences, rounded to BF16
-    }
-    const int w = r * LD + 4 * chunk_pos(g, r);
-    if (P == 4) {
-      *reinterpret_cast<uint4 *>(s.hi + w) = make_uint4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<uint4 *>(s.lo + w) = make_uint4(e[0], e[1], e[2], e[3]);
-    } else {
-      *reinterpret_cast<uint2 *>(s.hi + w) = make_uint2(h[0], h[1]);
-      *reinterpret_cast<uint2 *>(s.lo + w) = make_uint2(e[0], e[1]);
-    }
+  for (int c = 0; c < USED; ++c) {
+    const float2 x = col[c];
+    const uint32_t h = pack_bf16x2(x.x, x.y);
+    const float hx = __uint_as_float(h << 16), hy = __uint_as_float(h & 0xFFFF0000u);
+    const uint32_t e = pack_bf16x2(x.x - hx, x.y - hy);  // exact differences, rounded to BF16
+    *reinterpret_cast<uint32_t *>(region + c * kRowBytes + offs[c & 7]) = h;
+    *reinterpret_cast<uint32_t *>(region + (NC + c) * kRowBytes + offs[(NC + c) & 7]) = e;
   }
 }
 
-// One warp's FP32 fragments of the upper block-triangle of G.
+// Issues the tile's MMAs (one thread): GROUPS operands of 128 rows, 4 K-steps of 16 sites
+// (32 bytes inside the 128-byte swizzle row) each; the first overwrites the accumulator
+// when `fresh`.
 template <int D>
-struct Warp {
-  using P = StatsPlan<D>;
-  float d[P::NTILE][4];
-  int off_a, off_b;  // word offsets of the lane's chunk in rows s0 + t and s0 + t + 4
+__device__ __forceinline__ void issue_tile(uint32_t buf_saddr, uint32_t tmem, bool fresh) {
+  using P = Plan<D>;
+#pragma unroll
+  for (int g = 0; g < P::GROUPS; ++g)
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const uint64_t desc = sw128_kmajor_desc(buf_saddr + (uint32_t)(g * 128 * kRowBytes + kk * 32));
+      mma_bf16(tmem, desc, desc, (fresh && g == 0 && kk == 0) ? 0u : 1u);
+    }
+}
 
-  __device__ __forceinline__ void init() {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int i = 0; i < P::NTILE; ++i)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) d[i][r] = 0.0f;
-    off_a = 4 * chunk_pos(g, t);
-    off_b = 4 * chunk_pos(g, t + 4);
-  }
+// Accumulator row of this thread: lane l of warp q holds TMEM lane 32 q + l, which is row
+// r = (32 q + l) mod 2 NC of a diagonal block starting at column 2 NC (32 q / 2 NC); row r
+// is column i = r mod NC of G (hi part for r < NC, lo part otherwise). Its contribution
+// slot (32 q + l) / NC (4 slots for NC = 32, 8 for NC = 16) is unique per (block, part, i).
+template <int D>
+struct Flush {
+  using P = Plan<D>;
+  static constexpr int NC = P::NC, SLOTS = 128 / NC, NREC = StatsPlan<D>::NREC;
+  static constexpr int PER_THREAD = (NREC + kStatsBlock - 1) / kStatsBlock;
+  uint32_t taddr;            // this lane's first accumulator column of its diagonal block
+  int slot, i;               // contribution slot and G column
+  int ent_off[PER_THREAD];   // scratch offset j NC + i of the record entries this thread owns
 
-  // This warp's 32 rows (64 sites) of the staged tile, 8 rows = 16 sites per MMA step (the
-  // K dimension); the caller has made its lanes' staging visible (__syncwarp). Rows s0 + t
-  // and s0 + t + 4 (s0 a multiple of 8) keep their chunk positions at every step, so the
-  // steps only move the row base. A fragments: a0, a1 = columns m0 + g, m0 + g + 8 of the
-  // site pair of row t (K indices 2t, 2t + 1); a2, a3 = the same columns of row t + 4
-  // (K indices 2t + 8, 2t + 9), m0 = 0, 16.
-  __device__ __forceinline__ void tile(const Smem<D> &s) {
-    const int warp = threadIdx.x >> 5, t = threadIdx.x & 3;
-    constexpr int LD = P::LD;
-#pragma unroll 2
-    for (int ks = 0; ks < 4; ++ks) {
-      const int ra = (warp * 32 + ks * 8 + t) * LD + off_a, rb = (warp * 32 + ks * 8 + t + 4) * LD + off_b;
-      uint32_t ah[P::MT][4], al[P::MT][4], bh[P::NT][2], bl[P::NT][2];
-      if (P::MT == 2) {
-        const uint4 ha = *reinterpret_cast<const uint4 *>(s.hi + ra), hb = *reinterpret_cast<const uint4 *>(s.hi + rb);
-        const uint4 la = *reinterpret_cast<const uint4 *>(s.lo + ra), lb = *reinterpret_cast<const uint4 *>(s.lo + rb);
-        ah[0][0] = ha.x; ah[0][1] = ha.y; ah[0][2] = hb.x; ah[0][3] = hb.y;
-        ah[P::MT - 1][0] = ha.z; ah[P::MT - 1][1] = ha.w; ah[P::MT - 1][2] = hb.z; ah[P::MT - 1][3] = hb.w;
-        al[0][0] = la.x; al[0][1] = la.y; al[0][2] = lb.x; al[0][3] = lb.y;
-        al[P::MT - 1][0] = la.z; al[P::MT - 1][1] = la.w; al[P::MT - 1][2] = lb.z; al[P::MT - 1][3] = lb.w;
-      } else {
-        const uint2 ha = *reinterpret_cast<const uint2 *>(s.hi + ra), hb = *reinterpret_cast<const uint2 *>(s.hi + rb);
-        const uint2 la = *reinterpret_cast<const uint2 *>(s.lo + ra), lb = *reinterpret_cast<const uint2 *>(s.lo + rb);
-        ah[0][0] = ha.x; ah[0][1] = ha.y; ah[0][2] = hb.x; ah[0][3] = hb.y;
-        al[0][0] = la.x; al[0][1] = la.y; al[0][2] = lb.x; al[0][3] = lb.y;
-      }
-      // G is symmetric (A = K^T, B = K): the B fragment of column tile nt is the pair
-      // (a0, a2) or (a1, a3) of row tile nt / 2, already loaded.
+  __device__ __forceinline__ void init(uint32_t tmem) {
+    const int q = threadIdx.x >> 5, grow = threadIdx.x;  // 32 q + lane
+    taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((grow / P::ROWS) * P::ROWS);
+    slot = grow / NC;
+    i = grow % NC;
+    // Record entry e = a NC - a (a - 1) / 2 + (b - a) is G(a, b), a <= b (row-major upper
+    // triangle); this thread owns e = threadIdx.x + k kStatsBlock.
 #pragma unroll
-      for (int nt = 0; nt < P::NT; ++nt) {
-        const int mt = nt / 2, h = nt % 2;
-        bh[nt][0] = ah[mt][h];
-        bh[nt][1] = ah[mt][h + 2];
-        bl[nt][0] = al[mt][h];
-        bl[nt][1] = al[mt][h + 2];
-      }
-      // hi*hi, hi*lo, lo*hi, then lo*lo over all tiles: consecutive MMAs go to different
-      // accumulators, so none waits for the one before it.
-#pragma unroll
-      for (int i = 0; i < P::NTILE; ++i) mma_bf16(d[i], ah[tile_mt<D>(i)], bh[tile_nt<D>(i)]);
-#pragma unroll
-      for (int i = 0; i < P::NTILE; ++i) mma_bf16(d[i], ah[tile_mt<D>(i)], bl[tile_nt<D>(i)]);
-#pragma unroll
-      for (int i = 0; i < P::NTILE; ++i) mma_bf16(d[i], al[tile_mt<D>(i)], bh[tile_nt<D>(i)]);
-#pragma unroll
-      for (int i = 0; i < P::NTILE; ++i) mma_bf16(d[i], al[tile_mt<D>(i)], bl[tile_nt<D>(i)]);
+    for (int k = 0; k < PER_THREAD; ++k) {
+      const int e = threadIdx.x + k * kStatsBlock;
+      int a = 0;
+      while (a + 1 < NC && (a + 1) * NC - (a + 1) * a / 2 <= e) ++a;
+      const int b = a + (e - (a * NC - a * (a - 1) / 2));
+      ent_off[k] = e < NREC ? b * NC + a : -1;
     }
   }
 
-  // Adds the fragments to the block's FP64 sums and clears them.
-  __device__ __forceinline__ void flush(const Smem<D> &s) {
-    const int lane = threadIdx.x & 31;
+  // Every thread of the block, after the MMAs of the closed period are done: each row goes
+  // to the scratch (FP32, [slot][j][i], in the idle staging rows), then the owner of each
+  // record entry adds the sum of its slots to the block's FP64 sums. `valid`: warp-uniform;
+  // a warp whose wait gave up skips its accumulator reads (the block then reports failure).
+  __device__ __forceinline__ void run(float *scratch, double *sums, bool valid) {
+    if (valid) {
 #pragma unroll
-    for (int i = 0; i < P::NTILE; ++i)
+      for (int j0 = 0; j0 < NC; j0 += 16) {
+        float hi[16], lo[16];
+        tmem_ld16(taddr + (uint32_t)j0, hi);
+        tmem_ld16(taddr + (uint32_t)(NC + j0), lo);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        atomicAdd(&s.acc64[(i * 4 + r) * 32 + lane], (double)d[i][r]);
-        d[i][r] = 0.0f;
+        for (int k = 0; k < 16; ++k) scratch[(slot * NC + j0 + k) * NC + i] = hi[k] + lo[k];
       }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER_THREAD; ++k) {
+      if (ent_off[k] < 0) continue;
+      float v = 0.0f;
+#pragma unroll
+      for (int sl = 0; sl < SLOTS; ++sl) v += scratch[sl * NC * NC + ent_off[k]];
+      sums[threadIdx.x + k * kStatsBlock] += (double)v;
+    }
+    __syncthreads();  // the scratch is staging memory again
   }
 };
 
-// After the block's last flush and a barrier: sums the warps' fragments and adds the
-// upper triangle of G (and the block's non-finite count) to the output record.
+// After the block's last flush and a barrier: adds its FP64 sums (in record order) and
+// its non-finite count, or the timeout mark, to the output record.
 template <int D>
-__device__ __forceinline__ void finish(const Smem<D> &s, unsigned nonfinite_block, double *__restrict__ acc) {
-  using P = StatsPlan<D>;
-  constexpr int NC = P::NC;
-  for (int e = threadIdx.x; e < P::NTILE * 4 * 32; e += blockDim.x) {
-    const int i = e / 128, r = (e / 32) % 4, ln = e % 32;
-    const int row = tile_mt<D>(i) * 16 + (ln >> 2) + (r >= 2 ? 8 : 0);
-    const int colx = tile_nt<D>(i) * 8 + 2 * (ln & 3) + (r & 1);
-    if (row > colx) continue;
-    atomicAdd(&acc[row * NC - row * (row - 1) / 2 + (colx - row)], s.acc64[e]);
+__device__ __forceinline__ void finish(const double *sums, unsigned nonfinite_block, bool failed,
+                                       double *__restrict__ out) {
+  constexpr int NREC = StatsPlan<D>::NREC;
+  for (int e = threadIdx.x; e < NREC; e += blockDim.x) atomicAdd(&out[e], sums[e]);
+  if (threadIdx.x == 0) {
+    double mark = (double)nonfinite_block;
+    if (failed) mark += kStatsTimeoutMark;
+    if (mark != 0.0) atomicAdd(&out[NREC], mark);
   }
-  if (threadIdx.x == 0 && nonfinite_block) atomicAdd(&acc[P::NREC], (double)nonfinite_block);
 }
 
 }  // namespace gram

@@ -29,185 +29,244 @@ namespace {
 
 using gram::kTileSites;
 
-// The D3Q19 columns of two sites s, s + 1 (lattice code 19): [1, rho - rho0, j, u,
-// k_4 .. k_18, 0 ...] from the generated transforms of d3q19_gen.cuh.
-template <typename S, int PARITY, bool PAIRROW>
-__device__ __forceinline__ void pair_columns19(const S *__restrict__ f, long long plane, int nx, int ny, int nz,
-                                               float rho0, long long s, long long N, float2 *col,
-                                               unsigned &nonfinite) {
-  float2 F[19];
-  const bool valid[2] = {s < N, s + 1 < N};
-  if (PAIRROW) {
-    if (valid[0]) {
-      const uint32_t r = (uint32_t)s / (uint32_t)nx, q = r / (uint32_t)ny;
-      const int x0 = (int)((uint32_t)s - r * (uint32_t)nx), y = (int)(r - q * (uint32_t)ny), z = (int)q;
-      load19_pairs<S, PARITY>(f, plane, addr2(x0, y, z, nx, ny, nz), F);
-    } else {
-#pragma unroll
-      for (int a = 0; a < 19; ++a) F[a] = make_float2(0.0f, 0.0f);
-    }
-  } else {
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      const long long sl = s + l;
-      float Fl[19];
-      if (valid[l]) {
-        const uint32_t r = (uint32_t)sl / (uint32_t)nx, q = r / (uint32_t)ny;
-        const int x = (int)((uint32_t)sl - r * (uint32_t)nx), y = (int)(r - q * (uint32_t)ny), z = (int)q;
-        load19<S, PARITY>(f, plane, neighbourhood(x, y, z, nx, ny, nz), Fl);
-      } else {
-#pragma unroll
-        for (int a = 0; a < 19; ++a) Fl[a] = 0.0f;
-      }
-#pragma unroll
-      for (int a = 0; a < 19; ++a) set_lane(F[a], l, Fl[a]);
-    }
-  }
-  float2 r[19], rho, ux, uy, uz;
-  d3q19_macros(F, rho0, r, rho, ux, uy, uz);
-  const float2 drho = r[0];
-  d3q19_central(r, rho, ux, uy, uz);
-  col[0] = make_float2(valid[0] ? 1.0f : 0.0f, valid[1] ? 1.0f : 0.0f);
-  col[1] = drho;
-  col[2] = vmul(rho, ux);
-  col[3] = vmul(rho, uy);
-  col[4] = vmul(rho, uz);
-  col[5] = ux;
-  col[6] = uy;
-  col[7] = uz;
-#pragma unroll
-  for (int v = 4; v < 19; ++v) col[8 + v - 4] = r[v];
-  float2 sum = col[1];
-#pragma unroll
-  for (int c = 2; c < 8 + 15; ++c) sum = vadd(sum, col[c]);
-#pragma unroll
-  for (int l = 0; l < 2; ++l) {
-    if (valid[l] && !isfinite(lane(sum, l))) {
-      ++nonfinite;
-#pragma unroll
-      for (int c = 0; c < 8 + 15; ++c) set_lane(col[c], l, 0.0f);
-    }
-  }
-}
-
-// Columns of the two sites of a pair (lane x: site s, lane y: site s + 1). PAIRROW: nx is
-// even, so s (even) and s + 1 share a row and load as pairs; on odd parity the pair is the
-// step's (cm.cuh, load_pairs: sites s + 1 and s + 2 of the row), which covers the same sites.
-template <int D, typename S, int PARITY, bool PAIRROW, bool ISO>
-__device__ __forceinline__ void pair_columns(const S *__restrict__ f, long long plane, int nx, int ny, int nz,
-                                             float rho0, long long s, long long N,
-                                             float2 (&col)[StatsPlan<D>::NC], unsigned &nonfinite) {
+// The populations of a thread's site pair, as loaded for one tile and consumed by the
+// next: F19 for D3Q19 (lattice code 19), the 3x3x3 tile otherwise.
+template <int D>
+struct PairPops {
   float2 F[3][3][3];
-  bool valid[2] = {s < N, s + 1 < N};
+};
+template <>
+struct PairPops<19> {
+  float2 F[19];
+};
+
+// Loads the pair's populations (lane x: site s, lane y: site s + 1; zeros for a site
+// beyond N). PAIRROW: nx is even, so s (even) and s + 1 share a row and load as pairs; on
+// odd parity the pair is the step's (cm.cuh, load_pairs: sites s + 1 and s + 2 of the
+// row), which covers the same sites.
+template <int D, typename S, int PARITY, bool PAIRROW>
+__device__ __forceinline__ void load_pair(const S *__restrict__ f, long long plane, int nx, int ny, int nz,
+                                          long long s, long long N, PairPops<D> &P) {
+  constexpr int NP = D == 19 ? 19 : 27;
+  float2 *F = reinterpret_cast<float2 *>(&P.F);
   if (PAIRROW) {
-    if (valid[0]) {
+    if (s < N) {
       const uint32_t r = (uint32_t)s / (uint32_t)nx, q = r / (uint32_t)ny;
       const int x0 = (int)((uint32_t)s - r * (uint32_t)nx), y = (int)(r - q * (uint32_t)ny), z = (int)q;
-      load_pairs<D, S, PARITY>(f, plane, addr2(x0, y, z, nx, ny, nz), F);
+      if constexpr (D == 19)
+        load19_pairs<S, PARITY>(f, plane, addr2(x0, y, z, nx, ny, nz), P.F);
+      else
+        load_pairs<D, S, PARITY>(f, plane, addr2(x0, y, z, nx, ny, nz), P.F);
     } else {
 #pragma unroll
-      for (int a = 0; a < 27; ++a) (&F[0][0][0])[a] = make_float2(0.0f, 0.0f);
+      for (int a = 0; a < NP; ++a) F[a] = make_float2(0.0f, 0.0f);
     }
   } else {
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
       const long long sl = s + l;
-      float Fl[3][3][3];
-      if (valid[l]) {
+      float Fl[NP];
+      if (sl < N) {
         const uint32_t r = (uint32_t)sl / (uint32_t)nx, q = r / (uint32_t)ny;
         const int x = (int)((uint32_t)sl - r * (uint32_t)nx), y = (int)(r - q * (uint32_t)ny), z = (int)q;
-        load_logical<D, S, PARITY>(f, plane, neighbourhood(x, y, z, nx, ny, nz), Fl);
+        if constexpr (D == 19)
+          load19<S, PARITY>(f, plane, neighbourhood(x, y, z, nx, ny, nz), Fl);
+        else
+          load_logical<D, S, PARITY>(f, plane, neighbourhood(x, y, z, nx, ny, nz),
+                                     *reinterpret_cast<float(*)[3][3][3]>(Fl));
       } else {
 #pragma unroll
-        for (int a = 0; a < 27; ++a) (&Fl[0][0][0])[a] = 0.0f;
+        for (int a = 0; a < NP; ++a) Fl[a] = 0.0f;
       }
 #pragma unroll
-      for (int a = 0; a < 27; ++a) set_lane((&F[0][0][0])[a], l, (&Fl[0][0][0])[a]);
+      for (int a = 0; a < NP; ++a) set_lane(F[a], l, Fl[a]);
     }
   }
-  float2 drho, rho, ux, uy, uz;
-  site_central_moments<D>(F, rho0, drho, rho, ux, uy, uz);
-  gram::moment_columns<D, ISO>(F, drho, rho, ux, uy, uz, valid[0], valid[1], col, nonfinite);
 }
 
+// The columns of the pair from its populations. D3Q19: [1, rho - rho0, j, u, k_4 .. k_18,
+// 0 ...] from the generated transforms of d3q19_gen.cuh; D2Q9 / D3Q27: gram::moment_columns.
+template <int D, bool ISO>
+__device__ __forceinline__ void pair_columns(PairPops<D> &P, float rho0, bool v0, bool v1,
+                                             float2 (&col)[StatsPlan<D>::NC], unsigned &nonfinite) {
+  if constexpr (D == 19) {
+    float2 r[19], rho, ux, uy, uz;
+    d3q19_macros(P.F, rho0, r, rho, ux, uy, uz);
+    const float2 drho = r[0];
+    d3q19_central(r, rho, ux, uy, uz);
+    col[0] = make_float2(v0 ? 1.0f : 0.0f, v1 ? 1.0f : 0.0f);
+    col[1] = drho;
+    col[2] = vmul(rho, ux);
+    col[3] = vmul(rho, uy);
+    col[4] = vmul(rho, uz);
+    col[5] = ux;
+    col[6] = uy;
+    col[7] = uz;
+#pragma unroll
+    for (int v = 4; v < 19; ++v) col[8 + v - 4] = r[v];
+#pragma unroll
+    for (int c = 8 + 15; c < StatsPlan<D>::NC; ++c) col[c] = make_float2(0.0f, 0.0f);
+    float2 sum = col[1];
+#pragma unroll
+    for (int c = 2; c < 8 + 15; ++c) sum = vadd(sum, col[c]);
+    const bool valid[2] = {v0, v1};
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      if (valid[l] && !isfinite(lane(sum, l))) {
+        ++nonfinite;
+#pragma unroll
+        for (int c = 0; c < 8 + 15; ++c) set_lane(col[c], l, 0.0f);
+      }
+    }
+  } else {
+    float2 drho, rho, ux, uy, uz;
+    site_central_moments<D>(P.F, rho0, drho, rho, ux, uy, uz);
+    gram::moment_columns<D, ISO>(P.F, drho, rho, ux, uy, uz, v0, v1, col, nonfinite);
+  }
+}
+
+// 32-bit words of the rows of unused columns (hi and lo) over the block's staging.
+template <int D>
+__host__ __device__ constexpr int kWarpsTimesZeroWords() {
+  return gram::kWarps * 2 * (StatsPlan<D>::NC - StatsPlan<D>::USED) * (gram::kRowBytes / 4);
+}
+
+// One block walks tiles of kTileSites sites: every thread loads and transforms its site
+// pair and stages the split columns (gram.cuh); each warp then arrives once on `staged`
+// (after every lane's proxy fence and a warp barrier); thread 0 waits for the
+// whole tile, issues its MMAs and commits them to `bar`. Before a thread overwrites the
+// staging rows it waits for the MMAs that read them (one phase of each mbarrier per tile;
+// every wait bounded), so the loads and arithmetic of the next tile proceed while the
+// tensor cores work.
 template <int D, typename S, int PARITY, bool PAIRROW, bool ISO>
-__global__ void __launch_bounds__(kStatsBlock, PAIRROW ? 4 : 3) stats_kernel(const S *__restrict__ f, long long plane,
-                                                               int nx, int ny, int nz, float rho0,
-                                                               double *__restrict__ acc, long long site0,
+__global__ void __launch_bounds__(kStatsBlock, 4) stats_kernel(const S *__restrict__ f, long long plane, int nx,
+                                                               int ny, int nz, float rho0,
+                                                               double *__restrict__ out, long long site0,
                                                                long long site1) {
-  constexpr int NC = StatsPlan<D>::NC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const gram::Smem<D> sm = gram::smem_layout<D>(smem_raw);
+  using P = gram::Plan<D>;
+  constexpr int NC = P::NC, USED = StatsPlan<D>::USED;
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte aligned staging (the swizzle atoms), then the FP64 sums, mbarrier, TMEM address.
+  const uint32_t raw_s = smem_addr(smem_raw);
+  unsigned char *buf = smem_raw + (((raw_s + 1023u) & ~1023u) - raw_s);
+  double *sums = reinterpret_cast<double *>(buf + P::BUF);
+  uint64_t *staged = reinterpret_cast<uint64_t *>(sums + P::ACC);  // every warp, once per tile
+  uint64_t *bar = staged + 1;                                         // the tile's MMAs are done
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
   __shared__ unsigned int nonfinite_block;
-  if (threadIdx.x == 0) nonfinite_block = 0u;
-  gram::zero_acc64<D>(sm);
-  __syncthreads();  // sums zeroed before any warp flushes (warps do not meet again in the loop)
-  gram::Warp<D> gw;
-  gw.init();
+  __shared__ int failed_block;
+
+  const int warp = threadIdx.x >> 5;
+  unsigned char *region = buf + warp * P::REGION;
+  if (warp == 0) gram::tmem_alloc(tslot);
+  if (threadIdx.x == 0) {
+    nonfinite_block = 0u;
+    failed_block = 0;
+    mbar_init(staged, gram::kWarps);
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  for (int e = threadIdx.x; e < P::ACC; e += blockDim.x) sums[e] = 0.0;
+  // Rows of the unused columns (hi and lo) stay zero for the whole kernel.
+  for (int e = threadIdx.x; e < kWarpsTimesZeroWords<D>(); e += blockDim.x) {
+    constexpr int ZR = NC - USED, W = gram::kRowBytes / 4;
+    const int w = e / (2 * ZR * W), rr = (e / W) % (2 * ZR), k = e % W;
+    const int row = rr < ZR ? USED + rr : NC + USED + (rr - ZR);
+    reinterpret_cast<uint32_t *>(buf + w * P::REGION + row * gram::kRowBytes)[k] = 0u;
+  }
+  gram::fence_async_smem();
+  gram::tc_fence_before();
+  __syncthreads();
+  gram::tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t buf_s = smem_addr(buf);
+  uint32_t offs[8];
+  gram::stage_offsets(offs);
+  gram::Flush<D> fl;
+  fl.init(tmem);
 
   unsigned nonfinite = 0u;
+  bool ok = true;
   const long long N = site1;  // sites [site0, site1) of the array (plane = its Q-stride)
-  int tiles_done = 0;
-  for (long long base = site0 + (long long)blockIdx.x * kTileSites; base < N;
-       base += (long long)gridDim.x * kTileSites) {
+  const long long stride = (long long)gridDim.x * kTileSites;
+  int t = 0;
+  for (long long base = site0 + (long long)blockIdx.x * kTileSites; base < N; base += stride, ++t) {
     {
+      const long long s = base + 2 * threadIdx.x;
+      PairPops<D> pp;
+      load_pair<D, S, PARITY, PAIRROW>(f, plane, nx, ny, nz, s, N, pp);
       float2 col[NC];
-      if constexpr (D == 19) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) col[c] = make_float2(0.0f, 0.0f);
-        pair_columns19<S, PARITY, PAIRROW>(f, plane, nx, ny, nz, rho0, base + 2 * threadIdx.x, N, col,
-                                           nonfinite);
-      } else {
-        pair_columns<D, S, PARITY, PAIRROW, ISO>(f, plane, nx, ny, nz, rho0, base + 2 * threadIdx.x, N, col,
-                                                 nonfinite);
+      pair_columns<D, ISO>(pp, rho0, s < N, s + 1 < N, col, nonfinite);
+      if (t > 0) {
+        // The MMAs of the previous tile are done (phase t - 1): they have read the staging
+        // rows, and when they closed an accumulation period the accumulator is read now,
+        // before this tile's first MMA (issued after every thread has arrived below)
+        // overwrites it.
+        if (ok) ok = mbar_wait_bounded(bar, (uint32_t)(t - 1) & 1u);
+        if ((t - 1) % gram::kFlushTiles == gram::kFlushTiles - 1) {
+          ok = __all_sync(0xFFFFFFFFu, ok);  // the accumulator reads are warp-wide (.sync.aligned)
+          gram::tc_fence_after();
+          fl.run(reinterpret_cast<float *>(buf), sums, ok);
+        }
       }
-      // The thread's site pair in the warp's own rows; the rows are consumed (second
-      // __syncwarp) before the next tile overwrites them.
-      gram::stage_columns<D>(sm, col);
-      __syncwarp();
-      gw.tile(sm);
-      __syncwarp();
+      gram::stage_columns<D, USED>(region, offs, col);
     }
-    if (++tiles_done == gram::kFlushTiles) {
-      tiles_done = 0;
-      gw.flush(sm);
+    gram::fence_async_smem();  // each thread's rows, for the tensor cores
+    gram::tc_fence_before();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) gram::mbar_arrive(staged);  // the warp's rows are staged
+    if (threadIdx.x == 0) {
+      if (ok) ok = mbar_wait_bounded(staged, (uint32_t)t & 1u);
+      gram::tc_fence_after();
+      if (ok) gram::issue_tile<D>(buf_s, tmem, t % gram::kFlushTiles == 0);
+      gram::mma_commit(bar);
     }
   }
-  gw.flush(sm);
+  // The last accumulation period (every block has at least one tile).
+  if (ok) ok = mbar_wait_bounded(bar, (uint32_t)(t - 1) & 1u);
+  ok = __all_sync(0xFFFFFFFFu, ok);
+  gram::tc_fence_after();
+  if (!ok) {
+    failed_block = 1;
+    mbar_wait_bounded(bar, (uint32_t)(t - 1) & 1u);  // the MMAs in flight, bounded again
+  }
+  fl.run(reinterpret_cast<float *>(buf), sums, ok);
+  gram::tc_fence_before();
   if (nonfinite) atomicAdd(&nonfinite_block, nonfinite);
   __syncthreads();
-  gram::finish<D>(sm, nonfinite_block, acc);
+  if (warp == 0) {
+    gram::tc_fence_after();
+    gram::tmem_dealloc(tmem);
+  }
+  gram::finish<D>(sums, nonfinite_block, failed_block != 0, out);
 }
 
 template <int D, typename S>
 size_t stats_smem() {
-  return gram::smem_bytes<D>();
+  return gram::Plan<D>::SMEM;
 }
 
-// Resident blocks per SM for a kernel and its dynamic shared memory (cached; the
-// attribute that allows more than 48 KB is set once per kernel).
+// Persistent grid: gram::kBlocksPerSm blocks per SM, the residency the kernel is built for
+// (launch bounds of four blocks, 52 KB of shared memory and 128 of the SM's 512 TMEM
+// columns per block), at most one block per tile. The attribute that allows more than
+// 48 KB of dynamic shared memory is set once per kernel.
 template <typename K>
 cudaError_t stats_grid(K kernel, size_t smem, long long tiles, int *grid) {
   static std::mutex mu;
-  static std::map<const void *, int> cache;
-  int per_sm = 0;
+  static std::map<const void *, bool> ready;
   {
     std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find((const void *)kernel);
-    if (it != cache.end()) {
-      per_sm = it->second;
-    } else {
-      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kStatsBlock, smem);
+    if (!ready[(const void *)kernel]) {
+      const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      cache[(const void *)kernel] = per_sm;
+      ready[(const void *)kernel] = true;
     }
   }
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const long long cap = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  const long long cap = (long long)(sms > 0 ? sms : 1) * gram::kBlocksPerSm;
   *grid = (int)(tiles < cap ? tiles : cap);
   return cudaSuccess;
 }
