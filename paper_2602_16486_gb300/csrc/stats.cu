@@ -249,23 +249,24 @@ size_t stats_smem() {
 // Persistent grid: gram::kBlocksPerSm blocks per SM, the residency the kernel is built for
 // (launch bounds of four blocks, 52 KB of shared memory and 128 of the SM's 512 TMEM
 // columns per block), at most one block per tile. The attribute that allows more than
-// 48 KB of dynamic shared memory is set once per kernel.
+// 48 KB of dynamic shared memory is set once per kernel and device.
 template <typename K>
 cudaError_t stats_grid(K kernel, size_t smem, long long tiles, int *grid) {
   static std::mutex mu;
-  static std::map<const void *, bool> ready;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (!ready[(const void *)kernel]) {
-      const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      ready[(const void *)kernel] = true;
-    }
-  }
+  static std::map<std::pair<int, const void *>, bool> ready;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    bool &done = ready[std::make_pair(dev, (const void *)kernel)];
+    if (!done) {
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      done = true;
+    }
+  }
   const long long cap = (long long)(sms > 0 ? sms : 1) * gram::kBlocksPerSm;
   *grid = (int)(tiles < cap ? tiles : cap);
   return cudaSuccess;

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <utility>
 
@@ -148,8 +149,10 @@ constexpr size_t kPipeMaxSmem = 200 * 1024;  // largest stage pair pipe_applicab
 template <typename K>
 cudaError_t grid_for(K kernel, int threads, size_t smem, long long rows, int *grid) {
   static std::mutex mu;
-  static std::map<std::pair<const void *, size_t>, int> cache;  // blocks per SM
-  const auto key = std::make_pair((const void *)kernel, smem);
+  static std::map<std::tuple<int, const void *, size_t>, int> cache;  // blocks per SM, per device
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return cudaGetLastError();
+  const auto key = std::make_tuple(cur, (const void *)kernel, smem);
   int per_sm = 0;
   {
     std::lock_guard<std::mutex> lock(mu);
