@@ -248,6 +248,30 @@ def test_stats_match_oracle_on_same_state(fl, oracle_mod):
                                    atol=1e-5 * np.outer(scale, scale).max())
 
 
+@pytest.mark.parametrize("steps", [12, 13])
+@pytest.mark.parametrize("lattice,dims", [(0, (512, 6, 1)), (1, (256, 6, 5)), (1, (512, 2, 3))])
+def test_stats_row_tiles_match_oracle(fl, oracle_mod, lattice, dims, steps):
+    # nx a multiple of the reduction's 256-site tile: every tile lies inside one row and the
+    # kernel takes y, z and the periodic offsets from the tile (both parities).
+    lam = _lam(lattice, 1.6)
+    u0 = (0.04, -0.02, 0.01)
+    with fl.Lattice(lattice, dims, lam, 1e-3, 1.0, 5) as lat:
+        lat.init_uniform(u0, 1e-3, 9)
+        lat.step(steps)
+        st = lat.stats()
+        f = lat.populations()
+    ref = oracle_mod.stats(lattice, dims, f)
+    n = np.prod(dims)
+    assert st["sites"] == n and st["nonfinite"] == 0
+    assert st["mass"] == pytest.approx(ref["mass"], rel=1e-7)
+    assert np.all(np.abs(np.asarray(st["u_mean"]) - ref["u_mean"])
+                  <= 1e-5 * np.abs(ref["u_mean"]) + 1e-9 + mean_tol(ref["uu"][:3], n))
+    assert np.all(np.abs(np.asarray(st["uu"]) - ref["uu"]) <= 1e-5 * np.abs(ref["uu"]) + uu_tol(ref["uu"], n))
+    scale = np.sqrt(np.abs(np.diag(ref["k_cov"])))
+    np.testing.assert_allclose(st["k_mean"], ref["k_mean"], atol=1e-5 * scale.max() + 1e-9)
+    np.testing.assert_allclose(st["k_cov"], ref["k_cov"], rtol=1e-4, atol=1e-5 * np.outer(scale, scale).max())
+
+
 def test_sample_ring_matches_stats(fl):
     lam = _lam(0, 1.25, 1.25)
     with fl.Lattice(0, (40, 30, 1), lam, 1e-4, 1.0, 1) as lat:
