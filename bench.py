@@ -337,6 +337,7 @@ def run_ours(args):
     if world == 1 and not args.no_extras:
         line["storage_widths"] = storage_widths(fl, torch, stream, dims, peaks["hbm_gbs"])
         line["other_lattices"] = other_lattices(fl, torch, stream, dims, peaks["hbm_gbs"])
+        line["noise_off"] = noise_off(fl, torch, stream, dims, peaks["hbm_gbs"], avg_kernel_ms)
         line["batched_ensemble"] = batched_ensemble(fl, torch, peaks["hbm_gbs"])
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
@@ -416,6 +417,23 @@ def other_lattices(fl, torch, stream, dims, peak):
                          "step_variant": variant, "achieved_gbs": round(gbs, 1),
                          "frac_of_hbm": round(gbs / peak, 4), "bytes_per_site": q * 8}
     return out
+
+
+def noise_off(fl, torch, stream, dims, peak, noisy_ms):
+    """The headline workload at k_BT = 0 (the kernels' noise-free instantiation: no Philox,
+    no Box-Muller, identical loads, transforms, relaxation and stores), FP32, the noisy
+    kernel's variant: the difference to the noisy step is the cost of the 23 normals per
+    site."""
+    sites = dims[0] * dims[1] * dims[2]
+    with fl.Lattice(fl.FLBM_D3Q27, dims, lam_d3q27(), 0.0, 1.0, SEED, cuda_stream=stream.cuda_stream) as lat:
+        lat.init_uniform(U0, AMP, SEED)
+        variant = lat.autotune(10)
+        lat.step(6)
+        ms = _event_time(torch, stream, lat.step, 200)
+    gbs = BYTES_PER_SITE * sites / (ms * 1e-3) / 1e9
+    return {"value": round(sites / (ms * 1e-3) / 1e9, 3), "unit": UNIT, "ms_per_step": round(ms, 5),
+            "step_variant": variant, "achieved_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4),
+            "noise_share_of_noisy_step": round(max(0.0, 1.0 - ms / noisy_ms), 4)}
 
 
 def batched_ensemble(fl, torch, peak, steps=200, calls=25):
@@ -605,7 +623,7 @@ def run_profile_workload(args):
     of --dims with the paper's rates (shear 1.6), four steps of --variant (default 2);
     batch: the 256-lattice ensemble, three steps of the per-step five-blocks form;
     step: the headline physics on a D3Q27 box of --dims in --storage (D2Q9 when the box has
-    nz = 1), four steps of --variant (default 5)."""
+    nz = 1), four steps of --variant (default 5); with --noise-off at k_BT = 0."""
     import torch
 
     import paper_2602_16486_gb300 as fl
@@ -621,7 +639,7 @@ def run_profile_workload(args):
     elif args.profile == "step":
         lattice = fl.FLBM_D2Q9 if dims[2] == 1 else fl.FLBM_D3Q27
         lam = _lam_for(lattice)
-        with fl.Lattice(lattice, dims, lam, KBT, 1.0, SEED, args.storage) as lat:
+        with fl.Lattice(lattice, dims, lam, 0.0 if args.noise_off else KBT, 1.0, SEED, args.storage) as lat:
             lat.variant = args.variant or 5
             lat.init_uniform(U0 if lattice else U0[:2] + (0.0,), AMP, SEED)
             lat.step(4)
@@ -662,6 +680,8 @@ def main(argv=None):
                    help="step-kernel variant (1-6); default 0 = autotune")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the 16-bit storage, other-lattice and batched-ensemble measurements")
+    p.add_argument("--noise-off", action="store_true",
+                   help="--profile step: k_BT = 0 (the kernels' noise-free instantiation)")
     p.add_argument("--storage", type=int, default=0, choices=[0, 1, 2],
                    help="storage of the --profile step workload: 0 FP32, 1 BF16, 2 FP16")
     p.add_argument("--profile", choices=["stats", "d3q19", "batch", "step"], default=None,
