@@ -227,13 +227,17 @@ int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storage, int pari
  * shared memory with bulk asynchronous copies (needs nx even, nx <= 512 and a
  * population row a multiple of 16 bytes; else it falls back to 2), 5 and 6 = 2 and 3
  * compiled for more resident blocks per SM to hide latency: five for the 3-D lattices
- * (at most 102 registers), eight for D2Q9 (at most 64). Variants 2-6 fall back to 1 when
- * nx is odd. The environment variable FLBM_STEP_VARIANT, read by flbm_create, sets the
- * initial choice.
- * flbm_autotune times every applicable variant over trial_steps steps on a copy of the
+ * (at most 102 registers), eight for D2Q9 (at most 64); 7 and 8 = 5 and 2 with blocks of
+ * four rows of 32 site pairs instead of one row of 128 (for rows shorter than 256 sites,
+ * which leave most of a one-row block idle). Variants 2-8 fall back to 1 when nx is odd.
+ * The environment variable FLBM_STEP_VARIANT, read by flbm_create, sets the initial
+ * choice.
+ * flbm_autotune times every applicable variant (7 and 8 only for nx < 256) over
+ * trial_steps steps on a copy of the
  * current state (restored afterwards: populations and step count are unchanged), keeps
  * the fastest for this context and caches the choice per (GPU model, lattice, storage,
- * nx parity, size class, noise on/off, rate structure) for the process; when the
+ * nx parity, size class, noise on/off, rate structure, collision model, nx < 256) for
+ * the process; when the
  * environment variable FLBM_AUTOTUNE_CACHE names a file, choices are also read from it
  * (at the first flbm_autotune call of the process) and appended to it (one
  * "key<TAB>variant" line per choice), so later processes skip the trials. Needs one extra

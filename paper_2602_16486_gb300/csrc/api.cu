@@ -721,14 +721,16 @@ int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
   if (c->slab) return fail(FLBM_ESTATE, "a slab is not tuned alone (its steps need halo exchanges)");
   if (trial_steps < 2) return fail(FLBM_EINVAL, "trial_steps must be >= 2");
   DeviceGuard g(c->device);
-  // Cache: one choice per (device, lattice, storage, nx parity, size class, noise).
+  // Cache: one choice per (device, lattice, storage, nx parity, size class, noise, rate
+  // structure, collision model, rows shorter than one block).
   cudaDeviceProp prop;
   FLBM_CUDA(cudaGetDeviceProperties(&prop, c->device));
   int size_class = 0;
   for (long long n = c->N; n > 1; n >>= 1) ++size_class;
   char key[320];
-  std::snprintf(key, sizeof(key), "%s|%d|%d|%d|%d|%d|%d|%d", prop.name, c->lattice, c->storage,
-                int(c->dims[0] % 2), size_class, c->kBT > 0.0 ? 1 : 0, c->shear ? 1 : 0, c->model);
+  std::snprintf(key, sizeof(key), "%s|%d|%d|%d|%d|%d|%d|%d|%d", prop.name, c->lattice, c->storage,
+                int(c->dims[0] % 2), size_class, c->kBT > 0.0 ? 1 : 0, c->shear ? 1 : 0, c->model,
+                c->dims[0] < 2 * kStepBlock ? 1 : 0);
   static std::mutex mu;
   static std::map<std::string, int> cache;
   static bool file_read = false;
@@ -776,12 +778,14 @@ int flbm_autotune(flbm_ctx *c, int trial_steps, int *chosen) {
       st = fail(FLBM_ECUDA, "autotune set-up: %s", cudaGetErrorString(cudaGetLastError()));
       break;
     }
-    const int candidates[6] = {kStepOneSite, kStepPair, kStepPairRolled, kStepPipelined, kStepPairOcc,
-                               kStepPairRolledOcc};
+    const int candidates[8] = {kStepOneSite, kStepPair,    kStepPairRolled,  kStepPipelined,
+                               kStepPairOcc, kStepPairRolledOcc, kStepPairOccRows, kStepPairRows};
     for (int v : candidates) {
       if (pair_variants_only(c->lattice) &&
           (v == kStepPairRolled || v == kStepPipelined || v == kStepPairRolledOcc))
         continue;
+      // Blocks of four rows only where a row is shorter than a one-row block's 256 sites.
+      if ((v == kStepPairOccRows || v == kStepPairRows) && c->dims[0] >= 2 * kStepBlock) continue;
       if (v != kStepOneSite && c->dims[0] % 2 != 0) continue;
       if (v == kStepPipelined && !pipe_applicable(c->D, c->storage, int(c->dims[0]))) continue;
       c->variant = v;

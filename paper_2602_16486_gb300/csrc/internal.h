@@ -114,8 +114,11 @@ enum StepVariant {
   kStepPipelined = 4,
   kStepPairOcc = 5,        // as 2, register cap for five blocks per SM (D3Q27)
   kStepPairRolledOcc = 6,  // as 3, register cap for five blocks per SM (D3Q27)
-  kStepVariantMax = 6
+  kStepPairOccRows = 7,    // as 5, blocks of kRowBlockRows rows x 32 pair slots (short rows)
+  kStepPairRows = 8,       // as 2, blocks of kRowBlockRows rows x 32 pair slots (short rows)
+  kStepVariantMax = 8
 };
+constexpr int kRowBlockRows = 4;  // rows per block of variants 7 and 8 (one row per warp)
 bool pipe_applicable(int D, int storage, int nx);
 // lattice: the public lattice id (0 D2Q9, 1 D3Q27, 2 D3Q27 isotropic, 3 D3Q19).
 cudaError_t launch_step(int lattice, int storage, int variant, int parity, bool noise, bool shear,

@@ -23,8 +23,10 @@
 //                  point step runs as packed FP32x2, population pairs move as one 8-byte
 //                  (FP32) or 4-byte (16-bit) access, per-population address offsets are
 //                  block-uniform; capped at 128 registers (4 blocks of 4 warps per SM)
-//                  or, for more warps, 102 (5 blocks; 3-D lattices) or 51 (10 blocks;
-//                  D2Q9); the noise loop is unrolled or rolled (smaller code).
+//                  or, for more warps, 102 (5 blocks; 3-D lattices) or 64 (8 blocks;
+//                  D2Q9); the noise loop is unrolled or rolled (smaller code); blocks
+//                  cover one row of 128 pair slots, or four rows of 32 (one per warp) for
+//                  rows shorter than 256 sites.
 // Warps touch contiguous runs of every population, so all accesses are coalesced (odd
 // steps are shifted by one element, which costs no extra DRAM traffic).
 #include "step_kernels.cuh"

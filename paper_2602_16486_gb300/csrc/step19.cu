@@ -1,7 +1,8 @@
 // The fused step on D3Q19 (Sec. II-C, "Lattice-agnostic construction and the D3Q19
 // example"): the collision of d3q19.cuh between the AA-pattern load and store, one site
 // per thread (step variant 1, any nx) or two sites per thread with packed FP32x2
-// arithmetic (variants 2 and 5, nx even; 5 allows one more resident block per SM than 2).
+// arithmetic (variants 2 and 5, nx even; 5 allows one more resident block per SM than 2;
+// 8 and 7 are 2 and 5 in blocks of four rows for short rows).
 #include <cuda_runtime.h>
 
 #include "d3q19.cuh"
@@ -24,11 +25,14 @@ __global__ void __launch_bounds__(kStepBlock) step19_kernel(const StepArgs a) {
   store19<S, PARITY>(f, a.plane, nb, F);
 }
 
-template <typename S, int PARITY, bool NOISE, bool SHEAR, int MINB>
+// RB rows per block as in step2_kernel (step_kernels.cuh).
+template <typename S, int PARITY, bool NOISE, bool SHEAR, int MINB, int RB = 1>
 __global__ void __launch_bounds__(kStepBlock, MINB) step19_2_kernel(const StepArgs a) {
-  const int x0 = 2 * (blockIdx.x * kStepBlock + threadIdx.x);
-  if (x0 >= a.nx) return;
-  const Addr2 ad = addr2(x0, blockIdx.y, blockIdx.z + a.z_lo, a.nx, a.ny, a.nz);
+  constexpr int BX = kStepBlock / RB;
+  const int x0 = 2 * (blockIdx.x * BX + (RB == 1 ? (int)threadIdx.x : (int)threadIdx.x % BX));
+  const int y = RB == 1 ? (int)blockIdx.y : (int)blockIdx.y * RB + (int)threadIdx.x / BX;
+  if (x0 >= a.nx || y >= a.ny) return;
+  const Addr2 ad = addr2(x0, y, blockIdx.z + a.z_lo, a.nx, a.ny, a.nz);
   S *__restrict__ f = static_cast<S *>(a.f);
   float2 F[19];
   load19_pairs<S, PARITY>(f, a.plane, ad, F);
@@ -47,7 +51,13 @@ cudaError_t launch19(int variant, const StepArgs &a, cudaStream_t s) {
     // The general rates hold every central moment through the collision: their two-site
     // kernel gets a 168-register cap (three blocks per SM) instead of spilling.
     constexpr int kMinb = SHEAR ? 4 : 3;
-    if (variant == kStepPairOcc || variant == kStepPairRolledOcc)
+    constexpr int BX = kStepBlock / kRowBlockRows;
+    const dim3 grid_r((a.nx / 2 + BX - 1) / BX, (a.ny + kRowBlockRows - 1) / kRowBlockRows, a.nz_grid);
+    if (variant == kStepPairOccRows)
+      step19_2_kernel<S, PARITY, NOISE, SHEAR, kMinb + 1, kRowBlockRows><<<grid_r, block, 0, s>>>(a);
+    else if (variant == kStepPairRows)
+      step19_2_kernel<S, PARITY, NOISE, SHEAR, kMinb, kRowBlockRows><<<grid_r, block, 0, s>>>(a);
+    else if (variant == kStepPairOcc || variant == kStepPairRolledOcc)
       step19_2_kernel<S, PARITY, NOISE, SHEAR, kMinb + 1><<<grid, block, 0, s>>>(a);
     else
       step19_2_kernel<S, PARITY, NOISE, SHEAR, kMinb><<<grid, block, 0, s>>>(a);

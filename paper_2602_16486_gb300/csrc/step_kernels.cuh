@@ -29,11 +29,16 @@ __global__ void __launch_bounds__(kStepBlock) step_kernel(const StepArgs a) {
   store_streamed<D, S, PARITY>(f, a.plane, nb, F);
 }
 
-template <int D, typename S, int PARITY, bool NOISE, bool ROLLED, bool SHEAR, int MINB, bool ISO, bool RAW = false>
+// RB rows per block: 1 (128 pair slots of one row; y block-uniform) or kRowBlockRows
+// (each warp one row of 32 pair slots, for rows shorter than 256 sites).
+template <int D, typename S, int PARITY, bool NOISE, bool ROLLED, bool SHEAR, int MINB, bool ISO, bool RAW = false,
+          int RB = 1>
 __global__ void __launch_bounds__(kStepBlock, MINB) step2_kernel(const StepArgs a) {
-  const int x0 = 2 * (blockIdx.x * kStepBlock + threadIdx.x);
-  if (x0 >= a.nx) return;
-  const Addr2 ad = addr2(x0, blockIdx.y, blockIdx.z + a.z_lo, a.nx, a.ny, a.nz);
+  constexpr int BX = kStepBlock / RB;
+  const int x0 = 2 * (blockIdx.x * BX + (RB == 1 ? (int)threadIdx.x : (int)threadIdx.x % BX));
+  const int y = RB == 1 ? (int)blockIdx.y : (int)blockIdx.y * RB + (int)threadIdx.x / BX;
+  if (x0 >= a.nx || y >= a.ny) return;
+  const Addr2 ad = addr2(x0, y, blockIdx.z + a.z_lo, a.nx, a.ny, a.nz);
   S *__restrict__ f = static_cast<S *>(a.f);
 
   float2 F[3][3][3];
@@ -64,7 +69,14 @@ cudaError_t launch_kernel(int variant, const StepArgs &a, cudaStream_t s) {
     const dim3 grid((a.nx / 2 + kStepBlock - 1) / kStepBlock, a.ny, a.nz_grid);
     const bool occ = variant == kStepPairOcc || variant == kStepPairRolledOcc;
     const bool rolled = !ISO && (variant == kStepPairRolled || variant == kStepPairRolledOcc);
-    if (occ) {
+    if (variant == kStepPairOccRows || variant == kStepPairRows) {
+      constexpr int BX = kStepBlock / kRowBlockRows;
+      const dim3 grid_r((a.nx / 2 + BX - 1) / BX, (a.ny + kRowBlockRows - 1) / kRowBlockRows, a.nz_grid);
+      if (variant == kStepPairOccRows)
+        step2_kernel<D, S, PARITY, NOISE, false, SHEAR, kOcc, ISO, false, kRowBlockRows><<<grid_r, block, 0, s>>>(a);
+      else
+        step2_kernel<D, S, PARITY, NOISE, false, SHEAR, 4, ISO, false, kRowBlockRows><<<grid_r, block, 0, s>>>(a);
+    } else if (occ) {
       if (rolled)
         step2_kernel<D, S, PARITY, NOISE, !ISO, SHEAR, kOcc, ISO><<<grid, block, 0, s>>>(a);
       else

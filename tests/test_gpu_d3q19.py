@@ -59,12 +59,12 @@ def test_d3q19_init_matches_oracle_equilibrium(fl, oracle_mod):
 
 
 @pytest.mark.parametrize("variant,dims", [(1, (33, 8, 6)), (1, (64, 9, 7)), (2, (64, 9, 7)), (3, (64, 9, 7)),
-                                          (5, (64, 9, 7))])
+                                          (5, (64, 9, 7)), (7, (64, 9, 7)), (8, (40, 6, 5))])
 def test_d3q19_paper_rates_match_oracle(fl, oracle_mod, variant, dims):
     assert _run(fl, oracle_mod, dims, _paper_rates(1.6), 3e-4, 41, 100, variant) <= TOL
 
 
-@pytest.mark.parametrize("variant,dims", [(1, (33, 8, 6)), (2, (64, 9, 7)), (5, (64, 9, 7))])
+@pytest.mark.parametrize("variant,dims", [(1, (33, 8, 6)), (2, (64, 9, 7)), (5, (64, 9, 7)), (7, (64, 9, 7))])
 def test_d3q19_general_rates_match_oracle(fl, oracle_mod, variant, dims):
     assert _run(fl, oracle_mod, dims, _general_rates(), 1e-4, 42, 100, variant) <= TOL
 

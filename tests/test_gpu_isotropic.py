@@ -45,7 +45,7 @@ def _general_rates():
     return lam
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 5])
+@pytest.mark.parametrize("variant", [1, 2, 3, 5, 7, 8])
 def test_iso_general_rates_match_oracle(fl, oracle_mod, variant):
     assert _run(fl, oracle_mod, (64, 9, 7), _general_rates(), 1e-4, 21, 100, variant) <= TOL
 

@@ -76,7 +76,7 @@ def test_d2q9_64x64_fp64_config_parity(fl, oracle_mod):
     assert _err(fg, fo, 0) <= TOL
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_d3q27_drift_perturbed_ragged_box(fl, oracle_mod, variant):
     # The headline workload's physics (drift (0.05, 0.02, 0), 1e-3 density perturbation,
     # kBT = 1e-4, shear omega = 1.6) on a box spanning three x-blocks (one site per thread)
@@ -85,6 +85,35 @@ def test_d3q27_drift_perturbed_ragged_box(fl, oracle_mod, variant):
     f0, fg, fo = _run_pair(fl, oracle_mod, 1, (300, 7, 5), lam, 1e-4, 0, 100, (0.05, 0.02, 0.0),
                            1e-3, 0, variant=variant)
     assert _err(fg, fo, 1) <= TOL
+
+
+@pytest.mark.parametrize("variant,storage,dims", [(7, 0, (40, 9, 6)), (8, 0, (40, 9, 6)), (7, 0, (70, 5, 3)),
+                                                   (7, 1, (40, 9, 6)), (8, 2, (24, 13, 4))])
+def test_d3q27_row_blocks_narrow_box(fl, oracle_mod, variant, storage, dims):
+    # Blocks of four rows (variants 7, 8) on boxes whose rows are shorter than a one-row
+    # block, with a ragged last row group (ny not a multiple of 4) and a row longer than
+    # one warp's 64 sites; FP32 to the population tolerance, 16-bit storage one step against
+    # the rounding bound of its width.
+    lam = _lam(1, 1.6)
+    if storage == 0:
+        f0, fg, fo = _run_pair(fl, oracle_mod, 1, dims, lam, 2e-4, 11, 60, (0.05, 0.02, -0.01), 1e-3, 3,
+                               variant=variant)
+        assert _err(fg, fo, 1) <= TOL
+        return
+    bits = 8 if storage == 1 else 11
+    c, w, _ = oracle_mod.tables(1)
+    with fl.Lattice(1, dims, lam, 2e-4, 1.0, 11, storage) as lat:
+        lat.variant = variant
+        assert lat.variant == variant
+        lat.init_uniform((0.05, 0.02, -0.01), 1e-3, 3)
+        lat.step(3)
+        f0 = lat.populations()
+        lat.step(1)
+        got = lat.populations()
+    ref = oracle_mod.run(1, dims, lam, 2e-4, 11, f0, 3, 1)
+    wq = w.reshape(-1, 1, 1, 1)
+    bound = np.abs(ref - wq) * 2.0 ** -bits * 1.01 + 2e-6 * np.abs(ref) + 3e-8
+    assert float((np.abs(got - ref) / bound).max()) <= 1.0
 
 
 def test_d3q27_general_rates(fl, oracle_mod):
@@ -96,7 +125,7 @@ def test_d3q27_general_rates(fl, oracle_mod):
     assert _err(fg, fo, 1) <= TOL
 
 
-@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6, 7])
 def test_d2q9_paper_rates(fl, oracle_mod, variant):
     # D2Q9 with the paper's rates (L_4 = L_5 = omega, every other mode 1): the
     # specialised path that forms only the shear central moments.
@@ -106,7 +135,7 @@ def test_d2q9_paper_rates(fl, oracle_mod, variant):
     assert _err(fg, fo, 0) <= TOL
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_d2q9_general_rates_ragged(fl, oracle_mod, variant):
     rng = np.random.default_rng(6)
     lam = np.ones(9)
@@ -164,7 +193,7 @@ def test_autotune_leaves_the_state_unchanged(fl):
         lat.step(3)
         before = lat.populations()
         chosen = lat.autotune(4)
-        assert chosen in (1, 2, 3, 4, 5, 6) and lat.variant == chosen
+        assert chosen in (1, 2, 3, 4, 5, 6, 7, 8) and lat.variant == chosen
         assert lat.step_count == 3
         assert np.array_equal(lat.populations(), before)
         lat.variant = 1
