@@ -60,9 +60,15 @@ constexpr int kWarps = kStatsBlock / 32;   // warps per block (one TMEM lane qua
 constexpr int kTileSites = 2 * kStatsBlock;  // two sites per thread
 constexpr int kRowBytes = 128;             // one staged row: 64 sites in BF16
 constexpr uint32_t kTmemCols = 128;        // the 128 x 128 FP32 accumulator
-// 52 KB per block: four blocks fit the SM's 228 KB of shared memory, five do not.
+// 52 KB per block: four blocks fit the SM's 228 KB of shared memory, five do not (each
+// block holds 128 of the SM's 512 TMEM columns).
 constexpr size_t kSmemFloor = 52 * 1024;
-constexpr int kBlocksPerSm = 512 / (int)kTmemCols;
+// Resident blocks per SM the kernel is built for (launch bounds and grid): three for the
+// 3-D lattices, whose prefetched populations need up to 170 registers, four for D2Q9.
+template <int D>
+__host__ __device__ constexpr int blocks_per_sm() {
+  return D == 2 ? 4 : 3;
+}
 constexpr int kFlushTiles = 8;  // FP32 sums over at most 8 tiles (1024 sites per accumulator entry)
 // Added to the non-finite count of the record when a bounded wait gave up (the host
 // reports FLBM_ETIMEOUT for a negative count).

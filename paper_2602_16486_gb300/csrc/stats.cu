@@ -131,15 +131,15 @@ __host__ __device__ constexpr int kWarpsTimesZeroWords() {
   return gram::kWarps * 2 * (StatsPlan<D>::NC - StatsPlan<D>::USED) * (gram::kRowBytes / 4);
 }
 
-// One block walks tiles of kTileSites sites: every thread loads and transforms its site
-// pair and stages the split columns (gram.cuh); each warp then arrives once on `staged`
+// One block walks tiles of kTileSites sites: every thread transforms its site pair
+// (loaded during the previous tile) and stages the split columns (gram.cuh); each warp then arrives once on `staged`
 // (after every lane's proxy fence and a warp barrier); thread 0 waits for the
 // whole tile, issues its MMAs and commits them to `bar`. Before a thread overwrites the
 // staging rows it waits for the MMAs that read them (one phase of each mbarrier per tile;
 // every wait bounded), so the loads and arithmetic of the next tile proceed while the
 // tensor cores work.
 template <int D, typename S, int PARITY, bool PAIRROW, bool ISO>
-__global__ void __launch_bounds__(kStatsBlock, 4) stats_kernel(const S *__restrict__ f, long long plane, int nx,
+__global__ void __launch_bounds__(kStatsBlock, gram::blocks_per_sm<D>()) stats_kernel(const S *__restrict__ f, long long plane, int nx,
                                                                int ny, int nz, float rho0,
                                                                double *__restrict__ out, long long site0,
                                                                long long site1) {
@@ -190,13 +190,19 @@ __global__ void __launch_bounds__(kStatsBlock, 4) stats_kernel(const S *__restri
   const long long N = site1;  // sites [site0, site1) of the array (plane = its Q-stride)
   const long long stride = (long long)gridDim.x * kTileSites;
   int t = 0;
+  // Software pipelining: the populations of the thread's pair in the next tile are loaded
+  // as soon as the current ones are consumed, so the loads are in flight while the thread
+  // splits and stages its columns and waits for the tensor cores.
+  PairPops<D> pp;
+  if (site0 + (long long)blockIdx.x * kTileSites < N)
+    load_pair<D, S, PARITY, PAIRROW>(f, plane, nx, ny, nz, site0 + (long long)blockIdx.x * kTileSites + 2 * threadIdx.x,
+                                     N, pp);
   for (long long base = site0 + (long long)blockIdx.x * kTileSites; base < N; base += stride, ++t) {
     {
       const long long s = base + 2 * threadIdx.x;
-      PairPops<D> pp;
-      load_pair<D, S, PARITY, PAIRROW>(f, plane, nx, ny, nz, s, N, pp);
       float2 col[NC];
       pair_columns<D, ISO>(pp, rho0, s < N, s + 1 < N, col, nonfinite);
+      if (base + stride < N) load_pair<D, S, PARITY, PAIRROW>(f, plane, nx, ny, nz, s + stride, N, pp);
       if (t > 0) {
         // The MMAs of the previous tile are done (phase t - 1): they have read the staging
         // rows, and when they closed an accumulation period the accumulator is read now,
@@ -246,12 +252,12 @@ size_t stats_smem() {
   return gram::Plan<D>::SMEM;
 }
 
-// Persistent grid: gram::kBlocksPerSm blocks per SM, the residency the kernel is built for
-// (launch bounds of four blocks, 52 KB of shared memory and 128 of the SM's 512 TMEM
-// columns per block), at most one block per tile. The attribute that allows more than
-// 48 KB of dynamic shared memory is set once per kernel and device.
+// Persistent grid: `per_sm` blocks per SM, the residency the kernel is built for (its
+// launch bounds, 52 KB of shared memory and 128 of the SM's 512 TMEM columns per block),
+// at most one block per tile. The attribute that allows more than 48 KB of dynamic shared
+// memory is set once per kernel and device.
 template <typename K>
-cudaError_t stats_grid(K kernel, size_t smem, long long tiles, int *grid) {
+cudaError_t stats_grid(K kernel, size_t smem, long long tiles, int per_sm, int *grid) {
   static std::mutex mu;
   static std::map<std::pair<int, const void *>, bool> ready;
   int dev = 0, sms = 0;
@@ -267,7 +273,7 @@ cudaError_t stats_grid(K kernel, size_t smem, long long tiles, int *grid) {
       done = true;
     }
   }
-  const long long cap = (long long)(sms > 0 ? sms : 1) * gram::kBlocksPerSm;
+  const long long cap = (long long)(sms > 0 ? sms : 1) * per_sm;
   *grid = (int)(tiles < cap ? tiles : cap);
   return cudaSuccess;
 }
@@ -280,7 +286,7 @@ cudaError_t launch_one(const S *p, long long plane, int nx, int ny, int nz, floa
   const long long tiles = (nsites + kTileSites - 1) / kTileSites;
   if (tiles == 0) return cudaSuccess;
   int grid = 0;
-  const cudaError_t e = stats_grid(kernel, smem, tiles, &grid);
+  const cudaError_t e = stats_grid(kernel, smem, tiles, gram::blocks_per_sm<D>(), &grid);
   if (e != cudaSuccess) return e;
   kernel<<<grid, kStatsBlock, smem, s>>>(p, plane, nx, ny, nz, rho0, acc, site0, site0 + nsites);
   return cudaGetLastError();
