@@ -11,7 +11,9 @@ u0 = (0.05, 0.02, 0), kBT = 1e-4, shear rate omega = 1.6 (Lambda_7-9), all other
 Prints one JSON line (rank 0). N > 1 runs N independent replicas (one lattice per
 GPU, weak scaling, no data exchange) launched by torch.distributed.run. At N = 1 the
 line also carries the same workload with BF16 and FP16 deviation storage
-("storage_widths") and the 256-lattice batched ensemble ("batched_ensemble").
+("storage_widths"), on the isotropic D3Q27 variant and D3Q19 ("other_lattices"), at
+k_BT = 0 ("noise_off": the cost of the noise) and the 256-lattice batched ensemble
+("batched_ensemble").
 `--impl reference` times the FP64 CPU oracle on this host's cores on a bounded
 sample of the same workload.
 """
@@ -620,7 +622,8 @@ def run_reference(args):
 def run_profile_workload(args):
     """A short run of one kernel family for ncu captures (no timing, no bench line):
     stats: a D3Q27 box of --dims, two steps, two statistics reductions; d3q19: a D3Q19 box
-    of --dims with the paper's rates (shear 1.6), four steps of --variant (default 2);
+    of --dims with the paper's rates (shear 1.6), four steps of --variant (default 2), with
+    --noise-off at k_BT = 0;
     batch: the 256-lattice ensemble, three steps of the per-step five-blocks form;
     step: the headline physics on a D3Q27 box of --dims in --storage (D2Q9 when the box has
     nz = 1), four steps of --variant (default 5); with --noise-off at k_BT = 0."""
@@ -647,7 +650,7 @@ def run_profile_workload(args):
     elif args.profile == "d3q19":
         lam = np.ones(19)
         lam[[7, 8, 9]] = OMEGA
-        with fl.Lattice(fl.FLBM_D3Q19, dims, lam, KBT, 1.0, SEED) as lat:
+        with fl.Lattice(fl.FLBM_D3Q19, dims, lam, 0.0 if args.noise_off else KBT, 1.0, SEED) as lat:
             lat.variant = args.variant or 2
             lat.init_uniform(U0, AMP, SEED)
             lat.step(4)
@@ -681,7 +684,7 @@ def main(argv=None):
     p.add_argument("--no-extras", action="store_true",
                    help="skip the 16-bit storage, other-lattice and batched-ensemble measurements")
     p.add_argument("--noise-off", action="store_true",
-                   help="--profile step: k_BT = 0 (the kernels' noise-free instantiation)")
+                   help="--profile step / d3q19: k_BT = 0 (the kernels' noise-free instantiation)")
     p.add_argument("--storage", type=int, default=0, choices=[0, 1, 2],
                    help="storage of the --profile step workload: 0 FP32, 1 BF16, 2 FP16")
     p.add_argument("--profile", choices=["stats", "d3q19", "batch", "step"], default=None,
