@@ -373,3 +373,60 @@ def test_batch_zero_temperature_members(fl, oracle_mod):
         d = specs[i]
         fo = oracle_mod.run(d["lattice"], d["dims"], d["lam"], d["kBT"], d["seed"], f0[i], 0, 12)
         assert _err(got[i], fo, d["lattice"], d["rho0"]) <= TOL, i
+
+
+def test_c5_ensemble_full_size_sampled_members(fl, oracle_mod):
+    # The batched-ensemble workload at full size (256 lattices, 9.3 M sites, drawn as the
+    # benchmark draws them) in the launch shape the autotuner picks, as the benchmark times
+    # it: whole small members of both lattice types and both side parities against the
+    # oracle over three steps (both parities), and the largest D3Q27 members with an even
+    # and an odd side on sampled sites (their periodic seams among them) over one step.
+    import bench
+
+    specs = bench.draw_ensemble()
+    n = len(specs)
+    sizes = [int(np.prod(d["dims"])) for d in specs]
+    picks, bigs = [], []
+    for parity in (0, 1):
+        for lattice in (0, 1):
+            cand = [i for i in range(n) if specs[i]["lattice"] == lattice and specs[i]["dims"][0] % 2 == parity]
+            if cand:
+                picks.append(min(cand, key=lambda i: sizes[i]))
+                if lattice == 1:
+                    bigs.append(max(cand, key=lambda i: sizes[i]))
+    c, w, _ = oracle_mod.tables(1)
+    rng = np.random.default_rng(3)
+    samples = {}
+    for i in bigs:
+        nx, ny, nz = specs[i]["dims"]
+        xs, ys, zs = rng.integers(0, nx, 24), rng.integers(0, ny, 24), rng.integers(0, nz, 24)
+        xs[:4] = [0, nx - 1, 0, nx - 1]
+        ys[:4] = [0, ny - 1, ny - 1, 0]
+        zs[:4] = [nz - 1, 0, 0, nz - 1]
+        sites = xs + nx * (ys + ny * zs)
+        dests = [((x + c[:, 0]) % nx) + nx * (((y + c[:, 1]) % ny) + ny * ((z + c[:, 2]) % nz))
+                 for x, y, z in zip(xs, ys, zs)]
+        samples[i] = (sites, dests)
+    with fl.Batch(specs) as b:
+        for i in range(n):
+            b.lattice(i).init_uniform((0.0, 0.0, 0.0), 0.0, 0)
+        b.autotune(4)
+        b.step(2)
+        f0 = {i: b.lattice(i).populations() for i in picks}
+        pre = {i: b.lattice(i).sites_populations(samples[i][0]) for i in bigs}
+        b.step(1)
+        post = {i: [b.lattice(i).sites_populations(dst) for dst in samples[i][1]] for i in bigs}
+        b.step(2)
+        got = {i: b.lattice(i).populations() for i in picks}
+    for i in bigs:
+        d = specs[i]
+        worst = 0.0
+        for k, s in enumerate(samples[i][0]):
+            eta = oracle_mod.site_eta(1, d["seed"], 2, int(s))
+            fstar, _ = oracle_mod.collide_site(1, pre[i][k], d["lam"], d["kBT"], eta)
+            worst = max(worst, float((np.abs(post[i][k][np.arange(27), np.arange(27)] - fstar) / w).max()))
+        assert worst <= TOL, (i, d["dims"], worst)
+    for i in picks:
+        e = specs[i]
+        fo = oracle_mod.run(e["lattice"], e["dims"], e["lam"], e["kBT"], e["seed"], f0[i], 2, 3)
+        assert _err(got[i], fo, e["lattice"], e["rho0"]) <= TOL, (i, e["dims"])
