@@ -409,3 +409,41 @@ def test_pipelined_small_rows_fewer_threads_than_populations(fl, oracle_mod, lat
     f0, fg, fo = _run_pair(fl, oracle_mod, lattice, dims, lam, 1e-4, 12, 20, (0.02, 0.01, -0.01), 1e-3, 3,
                            variant=4)
     assert _err(fg, fo, lattice) <= TOL
+
+
+@pytest.mark.parametrize("pre_steps", [3, 4])
+@pytest.mark.parametrize("lattice", [2, 3])
+def test_full_size_other_lattices_sampled_sites(fl, oracle_mod, lattice, pre_steps):
+    # The benchmark's other lattices at 256^3 with its physics (drift, perturbation, kBT,
+    # shear rate 1.6; the isotropic variant's deviators at the shear rate too) in the
+    # launch configuration the autotuner picks there (variant 5): the oracle recomputes the
+    # collision of 32 sampled sites (the periodic seams among them) from the GPU's pre-step
+    # populations and compares it with what the GPU streamed into the neighbours.
+    dims = (256, 256, 256)
+    q = 27 if lattice == 2 else 19
+    lam = np.ones(q)
+    lam[[5, 6, 7, 8, 9] if lattice == 2 else [7, 8, 9]] = 1.6
+    c, w, _ = oracle_mod.tables(lattice)
+    rng = np.random.default_rng(10 + lattice)
+    nx, ny, nz = dims
+    xs, ys, zs = rng.integers(0, nx, 32), rng.integers(0, ny, 32), rng.integers(0, nz, 32)
+    xs[:4] = [0, nx - 1, 0, nx - 1]
+    ys[:4] = [0, ny - 1, ny - 1, 0]
+    zs[:4] = [nz - 1, 0, 0, nz - 1]
+    sites = xs + nx * (ys + ny * zs)
+    with fl.Lattice(lattice, dims, lam, 1e-4, 1.0, 0) as lat:
+        lat.variant = 5
+        assert lat.variant == 5
+        lat.init_uniform((0.05, 0.02, 0.0), 1e-3, 0)
+        lat.step(pre_steps)
+        pre = lat.sites_populations(sites)
+        lat.step(1)
+        worst = 0.0
+        for k, s in enumerate(sites):
+            x, y, z = xs[k], ys[k], zs[k]
+            eta = oracle_mod.site_eta(lattice, 0, pre_steps, int(s))
+            fstar, _ = oracle_mod.collide_site(lattice, pre[k], lam, 1e-4, eta)
+            dest = ((x + c[:, 0]) % nx) + nx * (((y + c[:, 1]) % ny) + ny * ((z + c[:, 2]) % nz))
+            got = lat.sites_populations(dest)[np.arange(q), np.arange(q)]
+            worst = max(worst, float((np.abs(got - fstar) / w).max()))
+    assert worst <= TOL, worst
