@@ -4,12 +4,12 @@
 // "Structural properties"), plus mass and momentum for the conservation checks.
 //
 // Every one of these sums is an entry of the Gram matrix G of the per-site columns
-// (gram.cuh: layout, BF16 four-pass tensor-core accumulation, output record; k_0 = rho
-// and the central moments k_1..k_D, which vanish identically, are rebuilt or set to zero
-// by the host, api.cu). Persistent blocks of kStatsBlock threads walk tiles of
-// 2 kStatsBlock sites: each thread computes the columns of two sites with the packed
-// FP32x2 algebra of the step (cm.cuh) and stages them in its warp's rows (one row per
-// pair, BF16 hi/lo words); each warp then accumulates the Gram fragments of its rows.
+// (gram.cuh: staging layout, BF16 hi/lo products on the tcgen05 tensor cores with a TMEM
+// accumulator, output record; k_0 = rho and the central moments k_1..k_D, which vanish
+// identically, are rebuilt or set to zero by the host, api.cu). Persistent blocks of
+// kStatsBlock threads walk tiles of 2 kStatsBlock sites: each thread computes the columns
+// of two sites with the packed FP32x2 algebra of the step (cm.cuh) and writes their BF16
+// hi/lo words into its warp's operand rows; one thread per block multiplies the tile.
 #include <cuda_runtime.h>
 
 #include <map>
