@@ -146,7 +146,7 @@ int64_t flbm_get_step(const flbm_ctx *ctx);
  * flbm_stats - statistics of the current state (velocity moments, Sec. III Eq. for
  * <u_a^2>; central-moment means and covariances, Sec. II-B C^eq), FP32 per site, the
  * products on the tensor cores (BF16 hi/lo splits of both factors, FP32 accumulation of
- * at most 512 sites, at most 2^-15 relative error per product and no bias) and FP64
+ * at most 1024 sites, at most 2^-15 relative error per product and no bias) and FP64
  * sums. Synchronises. Returns FLBM_ENUMERIC (and still fills *out) when some site is
  * not finite, FLBM_ETIMEOUT (out->nonfinite negative) if the reduction's bounded wait
  * for the tensor cores gave up.

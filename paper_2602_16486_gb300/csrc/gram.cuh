@@ -332,5 +332,110 @@ __device__ __forceinline__ void finish(const double *sums, unsigned nonfinite_bl
   }
 }
 
+// The block's side of the reduction, shared by the statistics kernel (stats.cu) and the
+// step kernel that takes a sample on the way (step_stats.cu): set-up (TMEM, mbarriers,
+// sums, the rows of unused columns), one call per tile that stages the thread's columns
+// and has one thread multiply the tile, and the end (last flush, record, TMEM freed). Every
+// thread of the block makes every call, in the same order.
+template <int D>
+struct Pipeline {
+  using P = Plan<D>;
+  static constexpr int NC = P::NC, USED = StatsPlan<D>::USED;
+  unsigned char *buf, *region;
+  double *sums;
+  uint64_t *staged, *bar;  // every warp once per tile / the tile's MMAs are done
+  uint32_t tmem, buf_s;
+  uint32_t offs[8];
+  Flush<D> fl;
+  bool ok;
+  int t;
+
+  // `raw`: the kernel's dynamic shared memory (P::SMEM bytes); `flags`: two shared words of
+  // the kernel (non-finite count, failure flag). Ends with a block barrier.
+  __device__ __forceinline__ void init(unsigned char *raw, unsigned int *flags) {
+    const uint32_t raw_s = smem_addr(raw);
+    buf = raw + (((raw_s + 1023u) & ~1023u) - raw_s);  // 1024-byte aligned swizzle atoms
+    sums = reinterpret_cast<double *>(buf + P::BUF);
+    staged = reinterpret_cast<uint64_t *>(sums + P::ACC);
+    bar = staged + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int warp = threadIdx.x >> 5;
+    region = buf + warp * P::REGION;
+    if (warp == 0) tmem_alloc(tslot);
+    if (threadIdx.x == 0) {
+      flags[0] = 0u;
+      flags[1] = 0u;
+      mbar_init(staged, kWarps);
+      mbar_init(bar, 1);
+      fence_mbar_init();
+    }
+    for (int e = threadIdx.x; e < P::ACC; e += blockDim.x) sums[e] = 0.0;
+    // Rows of the unused columns (hi and lo) stay zero for the whole kernel.
+    constexpr int ZR = NC - USED, W = kRowBytes / 4;
+    for (int e = threadIdx.x; e < kWarps * 2 * ZR * W; e += blockDim.x) {
+      const int w = e / (2 * ZR * W), rr = (e / W) % (2 * ZR), k = e % W;
+      const int row = rr < ZR ? USED + rr : NC + USED + (rr - ZR);
+      reinterpret_cast<uint32_t *>(buf + w * P::REGION + row * kRowBytes)[k] = 0u;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tmem = *tslot;
+    buf_s = smem_addr(buf);
+    stage_offsets(offs);
+    fl.init(tmem);
+    ok = true;
+    t = 0;
+  }
+
+  // One tile: waits for the previous tile's MMAs (they have read the staging rows; when
+  // they closed an accumulation period the accumulator is read now, before this tile's
+  // first MMA overwrites it), stages the columns, and thread 0 multiplies the tile once
+  // every warp has staged.
+  __device__ __forceinline__ void tile(const float2 (&col)[NC]) {
+    if (t > 0) {
+      if (ok) ok = mbar_wait_bounded(bar, (uint32_t)(t - 1) & 1u);
+      if ((t - 1) % kFlushTiles == kFlushTiles - 1) {
+        ok = __all_sync(0xFFFFFFFFu, ok);  // the accumulator reads are warp-wide (.sync.aligned)
+        tc_fence_after();
+        fl.run(reinterpret_cast<float *>(buf), sums, ok);
+      }
+    }
+    stage_columns<D, USED>(region, offs, col);
+    fence_async_smem();  // each thread's rows, for the tensor cores
+    tc_fence_before();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(staged);  // the warp's rows are staged
+    if (threadIdx.x == 0) {
+      if (ok) ok = mbar_wait_bounded(staged, (uint32_t)t & 1u);
+      tc_fence_after();
+      if (ok) issue_tile<D>(buf_s, tmem, t % kFlushTiles == 0);
+      mma_commit(bar);
+    }
+    ++t;
+  }
+
+  // After the last tile (t >= 1): the last accumulation period, the record, TMEM freed.
+  __device__ __forceinline__ void end(unsigned nonfinite, unsigned int *flags, double *__restrict__ out) {
+    if (ok) ok = mbar_wait_bounded(bar, (uint32_t)(t - 1) & 1u);
+    ok = __all_sync(0xFFFFFFFFu, ok);
+    tc_fence_after();
+    if (!ok) {
+      flags[1] = 1u;
+      mbar_wait_bounded(bar, (uint32_t)(t - 1) & 1u);  // the MMAs in flight, bounded again
+    }
+    fl.run(reinterpret_cast<float *>(buf), sums, ok);
+    tc_fence_before();
+    if (nonfinite) atomicAdd(&flags[0], nonfinite);
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+      tc_fence_after();
+      tmem_dealloc(tmem);
+    }
+    finish<D>(sums, flags[0], flags[1] != 0u, out);
+  }
+};
+
 }  // namespace gram
 }  // namespace flbm

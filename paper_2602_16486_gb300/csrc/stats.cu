@@ -125,71 +125,26 @@ __device__ __forceinline__ void pair_columns(PairPops<D> &P, float rho0, bool v0
   }
 }
 
-// 32-bit words of the rows of unused columns (hi and lo) over the block's staging.
-template <int D>
-__host__ __device__ constexpr int kWarpsTimesZeroWords() {
-  return gram::kWarps * 2 * (StatsPlan<D>::NC - StatsPlan<D>::USED) * (gram::kRowBytes / 4);
-}
-
 // One block walks tiles of kTileSites sites: every thread transforms its site pair
-// (loaded during the previous tile) and stages the split columns (gram.cuh); each warp then arrives once on `staged`
-// (after every lane's proxy fence and a warp barrier); thread 0 waits for the
-// whole tile, issues its MMAs and commits them to `bar`. Before a thread overwrites the
-// staging rows it waits for the MMAs that read them (one phase of each mbarrier per tile;
-// every wait bounded), so the loads and arithmetic of the next tile proceed while the
-// tensor cores work.
+// (loaded during the previous tile) and stages the split columns; each warp then arrives
+// once on the pipeline's "staged" mbarrier and thread 0 multiplies the tile (gram.cuh,
+// Pipeline). Before a thread overwrites the staging rows it waits for the MMAs that read
+// them (one phase of each mbarrier per tile; every wait bounded), so the loads and
+// arithmetic of the next tile proceed while the tensor cores work.
 template <int D, typename S, int PARITY, bool PAIRROW, bool ISO>
-__global__ void __launch_bounds__(kStatsBlock, gram::blocks_per_sm<D>()) stats_kernel(const S *__restrict__ f, long long plane, int nx,
-                                                               int ny, int nz, float rho0,
+__global__ void __launch_bounds__(kStatsBlock, gram::blocks_per_sm<D>()) stats_kernel(const S *__restrict__ f, long long plane,
+                                                               int nx, int ny, int nz, float rho0,
                                                                double *__restrict__ out, long long site0,
                                                                long long site1) {
-  using P = gram::Plan<D>;
-  constexpr int NC = P::NC, USED = StatsPlan<D>::USED;
+  constexpr int NC = StatsPlan<D>::NC;
   extern __shared__ unsigned char smem_raw[];
-  // 1024-byte aligned staging (the swizzle atoms), then the FP64 sums, mbarrier, TMEM address.
-  const uint32_t raw_s = smem_addr(smem_raw);
-  unsigned char *buf = smem_raw + (((raw_s + 1023u) & ~1023u) - raw_s);
-  double *sums = reinterpret_cast<double *>(buf + P::BUF);
-  uint64_t *staged = reinterpret_cast<uint64_t *>(sums + P::ACC);  // every warp, once per tile
-  uint64_t *bar = staged + 1;                                         // the tile's MMAs are done
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
-  __shared__ unsigned int nonfinite_block;
-  __shared__ int failed_block;
-
-  const int warp = threadIdx.x >> 5;
-  unsigned char *region = buf + warp * P::REGION;
-  if (warp == 0) gram::tmem_alloc(tslot);
-  if (threadIdx.x == 0) {
-    nonfinite_block = 0u;
-    failed_block = 0;
-    mbar_init(staged, gram::kWarps);
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  for (int e = threadIdx.x; e < P::ACC; e += blockDim.x) sums[e] = 0.0;
-  // Rows of the unused columns (hi and lo) stay zero for the whole kernel.
-  for (int e = threadIdx.x; e < kWarpsTimesZeroWords<D>(); e += blockDim.x) {
-    constexpr int ZR = NC - USED, W = gram::kRowBytes / 4;
-    const int w = e / (2 * ZR * W), rr = (e / W) % (2 * ZR), k = e % W;
-    const int row = rr < ZR ? USED + rr : NC + USED + (rr - ZR);
-    reinterpret_cast<uint32_t *>(buf + w * P::REGION + row * gram::kRowBytes)[k] = 0u;
-  }
-  gram::fence_async_smem();
-  gram::tc_fence_before();
-  __syncthreads();
-  gram::tc_fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t buf_s = smem_addr(buf);
-  uint32_t offs[8];
-  gram::stage_offsets(offs);
-  gram::Flush<D> fl;
-  fl.init(tmem);
+  __shared__ unsigned int flags[2];  // non-finite count of the block, failure flag
+  gram::Pipeline<D> pl;
+  pl.init(smem_raw, flags);
 
   unsigned nonfinite = 0u;
-  bool ok = true;
   const long long N = site1;  // sites [site0, site1) of the array (plane = its Q-stride)
   const long long stride = (long long)gridDim.x * kTileSites;
-  int t = 0;
   // Software pipelining: the populations of the thread's pair in the next tile are loaded
   // as soon as the current ones are consumed, so the loads are in flight while the thread
   // splits and stages its columns and waits for the tensor cores.
@@ -197,54 +152,14 @@ __global__ void __launch_bounds__(kStatsBlock, gram::blocks_per_sm<D>()) stats_k
   if (site0 + (long long)blockIdx.x * kTileSites < N)
     load_pair<D, S, PARITY, PAIRROW>(f, plane, nx, ny, nz, site0 + (long long)blockIdx.x * kTileSites + 2 * threadIdx.x,
                                      N, pp);
-  for (long long base = site0 + (long long)blockIdx.x * kTileSites; base < N; base += stride, ++t) {
-    {
-      const long long s = base + 2 * threadIdx.x;
-      float2 col[NC];
-      pair_columns<D, ISO>(pp, rho0, s < N, s + 1 < N, col, nonfinite);
-      if (base + stride < N) load_pair<D, S, PARITY, PAIRROW>(f, plane, nx, ny, nz, s + stride, N, pp);
-      if (t > 0) {
-        // The MMAs of the previous tile are done (phase t - 1): they have read the staging
-        // rows, and when they closed an accumulation period the accumulator is read now,
-        // before this tile's first MMA (issued after every thread has arrived below)
-        // overwrites it.
-        if (ok) ok = mbar_wait_bounded(bar, (uint32_t)(t - 1) & 1u);
-        if ((t - 1) % gram::kFlushTiles == gram::kFlushTiles - 1) {
-          ok = __all_sync(0xFFFFFFFFu, ok);  // the accumulator reads are warp-wide (.sync.aligned)
-          gram::tc_fence_after();
-          fl.run(reinterpret_cast<float *>(buf), sums, ok);
-        }
-      }
-      gram::stage_columns<D, USED>(region, offs, col);
-    }
-    gram::fence_async_smem();  // each thread's rows, for the tensor cores
-    gram::tc_fence_before();
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) gram::mbar_arrive(staged);  // the warp's rows are staged
-    if (threadIdx.x == 0) {
-      if (ok) ok = mbar_wait_bounded(staged, (uint32_t)t & 1u);
-      gram::tc_fence_after();
-      if (ok) gram::issue_tile<D>(buf_s, tmem, t % gram::kFlushTiles == 0);
-      gram::mma_commit(bar);
-    }
+  for (long long base = site0 + (long long)blockIdx.x * kTileSites; base < N; base += stride) {
+    const long long s = base + 2 * threadIdx.x;
+    float2 col[NC];
+    pair_columns<D, ISO>(pp, rho0, s < N, s + 1 < N, col, nonfinite);
+    if (base + stride < N) load_pair<D, S, PARITY, PAIRROW>(f, plane, nx, ny, nz, s + stride, N, pp);
+    pl.tile(col);
   }
-  // The last accumulation period (every block has at least one tile).
-  if (ok) ok = mbar_wait_bounded(bar, (uint32_t)(t - 1) & 1u);
-  ok = __all_sync(0xFFFFFFFFu, ok);
-  gram::tc_fence_after();
-  if (!ok) {
-    failed_block = 1;
-    mbar_wait_bounded(bar, (uint32_t)(t - 1) & 1u);  // the MMAs in flight, bounded again
-  }
-  fl.run(reinterpret_cast<float *>(buf), sums, ok);
-  gram::tc_fence_before();
-  if (nonfinite) atomicAdd(&nonfinite_block, nonfinite);
-  __syncthreads();
-  if (warp == 0) {
-    gram::tc_fence_after();
-    gram::tmem_dealloc(tmem);
-  }
-  gram::finish<D>(sums, nonfinite_block, failed_block != 0, out);
+  pl.end(nonfinite, flags, out);
 }
 
 template <int D, typename S>
