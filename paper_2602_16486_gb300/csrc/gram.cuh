@@ -332,11 +332,10 @@ __device__ __forceinline__ void finish(const double *sums, unsigned nonfinite_bl
   }
 }
 
-// The block's side of the reduction, shared by the statistics kernel (stats.cu) and the
-// step kernel that takes a sample on the way (step_stats.cu): set-up (TMEM, mbarriers,
-// sums, the rows of unused columns), one call per tile that stages the thread's columns
-// and has one thread multiply the tile, and the end (last flush, record, TMEM freed). Every
-// thread of the block makes every call, in the same order.
+// The block's side of the reduction (the statistics kernel, stats.cu): set-up (TMEM,
+// mbarriers, sums, the rows of unused columns), one call per tile that stages the thread's
+// columns and has one thread multiply the tile, and the end (last flush, record, TMEM
+// freed). Every thread of the block makes every call, in the same order.
 template <int D>
 struct Pipeline {
   using P = Plan<D>;
