@@ -233,15 +233,14 @@ int flbm_stats_noalloc(int lattice, const int64_t dims[3], int storage, int pari
  * The environment variable FLBM_STEP_VARIANT, read by flbm_create, sets the initial
  * choice.
  * flbm_autotune times every applicable variant (7 and 8 only for nx < 256) over
- * trial_steps steps on a copy of the
- * current state (restored afterwards: populations and step count are unchanged), keeps
- * the fastest for this context and caches the choice per (GPU model, lattice, storage,
- * nx parity, size class, noise on/off, rate structure, collision model, nx < 256) for
- * the process; when the
- * environment variable FLBM_AUTOTUNE_CACHE names a file, choices are also read from it
- * (at the first flbm_autotune call of the process) and appended to it (one
- * "key<TAB>variant" line per choice), so later processes skip the trials. Needs one extra
- * copy of the populations in device memory while it runs. Synchronises.
+ * trial_steps steps on a copy of the current state (restored afterwards: populations
+ * and step count are unchanged), keeps the fastest for this context and caches the
+ * choice per (GPU model, lattice, storage, nx parity, size class, noise on/off, rate
+ * structure, collision model, nx < 256) for the process; when the environment variable
+ * FLBM_AUTOTUNE_CACHE names a file, choices are also read from it (at the first
+ * flbm_autotune call of the process) and appended to it (one "key<TAB>variant" line per
+ * choice), so later processes skip the trials. Needs one extra copy of the populations
+ * in device memory while it runs. Synchronises.
  */
 int flbm_set_step_variant(flbm_ctx *ctx, int variant);
 int flbm_get_step_variant(const flbm_ctx *ctx);
