@@ -438,6 +438,10 @@ def noise_off(fl, torch, stream, dims, peak, noisy_ms):
             "noise_share_of_noisy_step": round(max(0.0, 1.0 - ms / noisy_ms), 4)}
 
 
+FORMS = ["per-step launches", "persistent launch", "per-step launches, 5 blocks/SM (D2Q9: 10)",
+         "per-step launches, rolled noise loop"]
+
+
 def batched_ensemble(fl, torch, peak, steps=200, calls=25):
     """The batched-ensemble workload in one batch (per-step graph-captured launches or one
     persistent launch, as the autotuner picks) against the same lattices stepped one
@@ -450,6 +454,7 @@ def batched_ensemble(fl, torch, peak, steps=200, calls=25):
         for i in range(len(specs)):
             b.lattice(i).init_uniform((0.0, 0.0, 0.0), 0.0, 0)
         threads, form = b.autotune(10)
+        threads2, form2 = b.type_shape(0)  # the D2Q9 lattices' own shape
         b.step(4)
         b.step(steps)  # capture of the timed call's graph
         b.sync()
@@ -482,8 +487,8 @@ def batched_ensemble(fl, torch, peak, steps=200, calls=25):
                         "tau 0.51..2.0, seeds 1000+j), FP32",
             "lattices": len(specs), "sites": sites, "value": round(sites / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
             "ms_per_step": round(ms, 5), "achieved_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4),
-            "steps": steps * calls, "threads": threads, "form": ["per-step launches", "persistent launch", "per-step launches, 5 blocks/SM",
-                                         "per-step launches, rolled noise loop"][form], "graph": graph,
+            "steps": steps * calls, "threads": threads, "form": FORMS[form],
+            "d2q9_threads": threads2, "d2q9_form": FORMS[form2], "graph": graph,
             "single_context_loop_ms_per_step": round(ms_loop, 5),
             "speedup_vs_single_context_loop": round(ms_loop / ms, 3),
             "timing": "wall clock around synchronised calls (own stream)"}

@@ -355,13 +355,23 @@ int64_t flbm_batch_get_step(const flbm_batch *b);
  *   2 per-step launches compiled for more resident blocks per SM: five for D3Q27 (up
  *     to 102 registers), ten for D2Q9 (up to 51); threads <= 128;
  *   3 per-step launches, up to 128 registers, D3Q27 noise loop rolled (smaller code).
- * flbm_batch_autotune times every (form, threads) pair over trial_steps steps (rounded
- * up to even) on a copy of the state (restored afterwards, step count unchanged), keeps
- * the fastest and returns it in *threads and *form (either may be NULL). Needs one extra
- * copy of all populations in device memory while it runs. Synchronises.
+ * flbm_batch_set_shape sets the shape of every lattice type; flbm_batch_get_shape
+ * returns the D3Q27 lattices' one. In the per-step forms each lattice type (FLBM_D2Q9,
+ * FLBM_D3Q27) launches separately and may take its own threads and per-step form
+ * (flbm_batch_set_type_shape: form 0, 2 or 3; FLBM_ESTATE while the batch is in the
+ * persistent form, which launches every type alike); flbm_batch_get_type_shape returns a
+ * type's shape as launched.
+ * flbm_batch_autotune times every (form, threads) pair for all lattices alike and then,
+ * in a per-step form, every per-step shape of the D2Q9 lattices with the D3Q27 lattices'
+ * shape fixed, over trial_steps steps each (rounded up to even) on a copy of the state
+ * (restored afterwards, step count unchanged); keeps the fastest and returns the D3Q27
+ * lattices' shape in *threads and *form (either may be NULL). Needs one extra copy of all
+ * populations in device memory while it runs. Synchronises.
  */
 int flbm_batch_set_shape(flbm_batch *b, int threads, int form);
 int flbm_batch_get_shape(const flbm_batch *b, int *threads, int *form);
+int flbm_batch_set_type_shape(flbm_batch *b, int lattice, int threads, int form);
+int flbm_batch_get_type_shape(const flbm_batch *b, int lattice, int *threads, int *form);
 int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads, int *form);
 
 /* 1 when the last flbm_batch_step replayed a captured graph, 0 when it launched

@@ -859,10 +859,12 @@ struct flbm_batch {
   std::vector<int> order;  // kernel table entry -> member (D3Q27 lattices first)
   BatchGroup g3{}, g2{};   // the two lattice types' table entries and tiles
   bool shear = true;       // every lattice follows the paper's rate structure
-  int threads = 128;       // block size; tiles hold 2 * threads sites
+  int threads = 128;       // block size of the D3Q27 lattices (all in the persistent form)
   int form = kBatchStep;    // enum BatchForm: per-step launches or one persistent launch
+  int threads2 = 128;      // the D2Q9 lattices' block size and per-step form (the
+  int form2 = kBatchStep;  // persistent form launches every type alike)
   int grid = 0;            // co-resident blocks (cooperative launch)
-  int tiles_for = 0;       // block size the tiling was built for
+  int tiles_for = 0, tiles_for2 = 0;  // block sizes the tiling was built for
   int ntiles = 0;
   float *d_rates = nullptr;  // om[27], phc[27] per lattice
   long long *d_step = nullptr;
@@ -952,12 +954,16 @@ int batch_params(flbm_batch *b) {
   return FLBM_OK;
 }
 
-// Tiling for the block size b->threads (tiles of `threads` pair slots, never spanning
-// lattices; a row of nx sites holds ceil(nx / 2) slots; lattice i owns tiles
-// [tile0_i, tile0_{i+1})) and the grid of co-resident blocks.
+// The D2Q9 lattices' block size and form as launched: their own in the per-step forms,
+// the batch's in the persistent one.
+int batch_threads2(const flbm_batch *b) { return b->form == kBatchPersistent ? b->threads : b->threads2; }
+int batch_form2(const flbm_batch *b) { return b->form == kBatchPersistent ? b->form : b->form2; }
+
+// Tiling for the block sizes (tiles of `threads` pair slots, never spanning lattices; a
+// row of nx sites holds ceil(nx / 2) slots; lattice i owns tiles [tile0_i, tile0_{i+1}))
+// and the grid of co-resident blocks.
 int batch_shape(flbm_batch *b) {
-  if (b->tiles_for == b->threads) return FLBM_OK;
-  const long long per_tile = b->threads;
+  if (b->tiles_for == b->threads && b->tiles_for2 == batch_threads2(b)) return FLBM_OK;
   long long total = 0;
   const int nl = int(b->members.size());
   int n3 = 0;  // table entries 0 .. n3-1 are the D3Q27 lattices
@@ -968,6 +974,7 @@ int batch_shape(flbm_batch *b) {
     b->args->lats[i].tile0 = int(total);
     const flbm_ctx *m = b->members[size_t(b->order[size_t(i)])];
     const long long slots = (m->dims[0] + 1) / 2 * m->dims[1] * m->dims[2];
+    const long long per_tile = m->D == 3 ? b->threads : batch_threads2(b);
     total += (slots + per_tile - 1) / per_tile;
     if (total > 0x3fffffffLL) return fail(FLBM_EINVAL, "too many tiles");
   }
@@ -985,6 +992,7 @@ int batch_shape(flbm_batch *b) {
   const long long g = (long long)per_sm * sms;
   b->grid = int(g < b->ntiles ? g : b->ntiles);
   b->tiles_for = b->threads;
+  b->tiles_for2 = batch_threads2(b);
   return FLBM_OK;
 }
 
@@ -995,7 +1003,8 @@ int batch_enqueue(flbm_batch *b, int64_t n) {
   b->args->pool = static_cast<char *>(b->pool);
   b->args->nlat = int(b->members.size());
   b->args->ntiles = b->ntiles;
-  b->args->tile_slots = b->threads;
+  b->args->tile_slots[1] = b->threads;
+  b->args->tile_slots[0] = batch_threads2(b);
   b->args->nsteps = int(n);
   b->args->step_counter = b->d_step;
   b->args->done = b->d_done;
@@ -1004,8 +1013,8 @@ int batch_enqueue(flbm_batch *b, int64_t n) {
   b->args->target_bias = b->test_wait_polls ? (1 << 30) : 0;
   b->args->wait_polls = b->test_wait_polls ? b->test_wait_polls : kBatchWaitPolls;
   if (b->form != kBatchPersistent) {
-    FLBM_CUDA(launch_batch_steps(b->form, b->shear, int(b->step & 1), *b->args, b->g3, b->g2, int(n), b->threads,
-                                 b->stream));
+    FLBM_CUDA(launch_batch_steps(b->form, b->threads, batch_form2(b), batch_threads2(b), b->shear, int(b->step & 1),
+                                 *b->args, b->g3, b->g2, int(n), b->stream));
     return FLBM_OK;
   }
   FLBM_CUDA(cudaMemsetAsync(b->d_done, 0, b->members.size() * sizeof(int), b->stream));
@@ -1175,7 +1184,7 @@ int flbm_batch_step(flbm_batch *b, int64_t n) {
     int st = batch_params(b);
     if (st != FLBM_OK) return st;
     batch_drop_graphs(b);
-    b->tiles_for = 0;  // the kernel form (shear) may have changed: new grid
+    b->tiles_for = b->tiles_for2 = 0;  // the kernel form (shear) may have changed: new grid
   }
   int st = batch_shape(b);
   if (st != FLBM_OK) return st;
@@ -1204,9 +1213,9 @@ int flbm_batch_set_shape(flbm_batch *b, int threads, int form) {
   if (form < 0 || form > kBatchFormMax) return fail(FLBM_EINVAL, "form = %d is not one of 0..%d", form, int(kBatchFormMax));
   if (form == kBatchStepOcc && threads > 128)
     return fail(FLBM_EINVAL, "form 2 (five blocks per SM) takes at most 128 threads per block");
-  if (threads != b->threads || form != b->form) batch_drop_graphs(b);
-  b->threads = threads;
-  b->form = form;
+  if (threads != b->threads || form != b->form || threads != b->threads2 || form != b->form2) batch_drop_graphs(b);
+  b->threads = b->threads2 = threads;
+  b->form = b->form2 = form;
   return FLBM_OK;
 }
 
@@ -1214,6 +1223,36 @@ int flbm_batch_get_shape(const flbm_batch *b, int *threads, int *form) {
   if (!b) return fail(FLBM_EINVAL, "batch is NULL");
   if (threads) *threads = b->threads;
   if (form) *form = b->form;
+  return FLBM_OK;
+}
+
+int flbm_batch_set_type_shape(flbm_batch *b, int lattice, int threads, int form) {
+  if (!b) return fail(FLBM_EINVAL, "batch is NULL");
+  if (lattice != FLBM_D2Q9 && lattice != FLBM_D3Q27)
+    return fail(FLBM_EINVAL, "lattice %d is not FLBM_D2Q9 (0) or FLBM_D3Q27 (1)", lattice);
+  if (b->form == kBatchPersistent)
+    return fail(FLBM_ESTATE, "the persistent form launches every lattice type alike (use flbm_batch_set_shape)");
+  if (threads == 0) threads = kBatchDefaultThreads;
+  if (threads != 64 && threads != 128 && threads != 256)
+    return fail(FLBM_EINVAL, "threads = %d must be 64, 128 or 256 (or 0)", threads);
+  if (form < 0 || form > kBatchFormMax || form == kBatchPersistent)
+    return fail(FLBM_EINVAL, "form = %d is not a per-step form (0, 2 or 3)", form);
+  if (form == kBatchStepOcc && threads > 128)
+    return fail(FLBM_EINVAL, "form 2 (five blocks per SM) takes at most 128 threads per block");
+  int &t = lattice == FLBM_D3Q27 ? b->threads : b->threads2;
+  int &f = lattice == FLBM_D3Q27 ? b->form : b->form2;
+  if (threads != t || form != f) batch_drop_graphs(b);
+  t = threads;
+  f = form;
+  return FLBM_OK;
+}
+
+int flbm_batch_get_type_shape(const flbm_batch *b, int lattice, int *threads, int *form) {
+  if (!b) return fail(FLBM_EINVAL, "batch is NULL");
+  if (lattice != FLBM_D2Q9 && lattice != FLBM_D3Q27)
+    return fail(FLBM_EINVAL, "lattice %d is not FLBM_D2Q9 (0) or FLBM_D3Q27 (1)", lattice);
+  if (threads) *threads = lattice == FLBM_D3Q27 ? b->threads : batch_threads2(b);
+  if (form) *form = lattice == FLBM_D3Q27 ? b->form : batch_form2(b);
   return FLBM_OK;
 }
 
@@ -1257,8 +1296,8 @@ int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads_out, int *f
   }
   const int64_t step0 = b->step;
   const long long step0_dev = (long long)step0;
-  const int saved_t = b->threads, saved_f = b->form;
-  int best_t = saved_t, best_f = saved_f, st = FLBM_OK;
+  const int saved_t = b->threads, saved_f = b->form, saved_t2 = b->threads2, saved_f2 = b->form2;
+  int best_t = saved_t, best_f = saved_f, best_t2 = saved_t2, best_f2 = saved_f2, st = FLBM_OK;
   float best = 1e30f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   // warm-up and capture of the timed shape (an even count keeps the start parity of the
@@ -1270,35 +1309,62 @@ int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads_out, int *f
       st = fail(FLBM_ECUDA, "autotune set-up: %s", cudaGetErrorString(cudaGetLastError()));
       break;
     }
+    // One trial: the shape (t3, f3) for the D3Q27 lattices (and every lattice in the
+    // persistent form) and (t2, f2) for the D2Q9 lattices, timed on the state copy.
+    auto trial = [&](int t3, int f3, int t2, int f2, float *ms) -> int {
+      b->threads = t3;
+      b->form = f3;
+      b->threads2 = t2;
+      b->form2 = f2;
+      batch_drop_graphs(b);
+      int r = flbm_batch_step(b, 2);
+      if (r == FLBM_OK) r = flbm_batch_step(b, nt);
+      if (r == FLBM_OK) {
+        cudaEventRecord(e0, b->stream);
+        r = flbm_batch_step(b, nt);
+      }
+      if (r == FLBM_OK) {
+        cudaEventRecord(e1, b->stream);
+        r = flbm_batch_sync(b);
+      }
+      if (r != FLBM_OK) return r;
+      cudaEventElapsedTime(ms, e0, e1);
+      b->step = step0;
+      for (flbm_ctx *c : b->members) c->step = step0;
+      if (cudaMemcpyAsync(b->pool, backup, b->pool_bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+          cudaMemcpyAsync(b->d_step, &step0_dev, sizeof(long long), cudaMemcpyHostToDevice, b->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return fail(FLBM_ECUDA, "autotune restore failed");
+      return FLBM_OK;
+    };
+    // Every lattice alike, then, in a per-step form, the D2Q9 lattices' own shape.
     for (int f = 0; f <= kBatchFormMax && st == FLBM_OK; ++f) {
       for (int t : {64, 128, 256}) {
         if (f == kBatchStepOcc && t > 128) continue;
-        b->threads = t;
-        b->form = f;
-        batch_drop_graphs(b);
-        if ((st = flbm_batch_step(b, 2)) != FLBM_OK) break;
-        if ((st = flbm_batch_step(b, nt)) != FLBM_OK) break;
-        cudaEventRecord(e0, b->stream);
-        if ((st = flbm_batch_step(b, nt)) != FLBM_OK) break;
-        cudaEventRecord(e1, b->stream);
-        if ((st = flbm_batch_sync(b)) != FLBM_OK) break;
         float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        if ((st = trial(t, f, t, f, &ms)) != FLBM_OK) break;
         if (ms < best) {
           best = ms;
-          best_t = t;
-          best_f = f;
+          best_t = best_t2 = t;
+          best_f = best_f2 = f;
         }
-        b->step = step0;
-        for (flbm_ctx *c : b->members) c->step = step0;
-        if (cudaMemcpyAsync(b->pool, backup, b->pool_bytes, cudaMemcpyDeviceToDevice, b->stream) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(b->d_step, &step0_dev, sizeof(long long), cudaMemcpyHostToDevice, b->stream) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(b->stream) != cudaSuccess) {
-          st = fail(FLBM_ECUDA, "autotune restore failed");
-          break;
+      }
+    }
+    if (st == FLBM_OK && best_f != kBatchPersistent && b->g2.ntiles > 0 && b->g3.ntiles > 0) {
+      const int t3 = best_t, f3 = best_f;
+      for (int f : {int(kBatchStep), int(kBatchStepOcc), int(kBatchStepRolled)}) {
+        for (int t : {64, 128, 256}) {
+          if ((f == kBatchStepOcc && t > 128) || (t == t3 && f == f3)) continue;
+          float ms = 0.0f;
+          if ((st = trial(t3, f3, t, f, &ms)) != FLBM_OK) break;
+          if (ms < best) {
+            best = ms;
+            best_t2 = t;
+            best_f2 = f;
+          }
         }
+        if (st != FLBM_OK) break;
       }
     }
   } while (false);
@@ -1312,10 +1378,14 @@ int flbm_batch_autotune(flbm_batch *b, int trial_steps, int *threads_out, int *f
   if (st != FLBM_OK) {
     b->threads = saved_t;
     b->form = saved_f;
+    b->threads2 = saved_t2;
+    b->form2 = saved_f2;
     return st;
   }
   b->threads = best_t;
   b->form = best_f;
+  b->threads2 = best_t2;
+  b->form2 = best_f2;
   if (threads_out) *threads_out = best_t;
   if (form_out) *form_out = best_f;
   return FLBM_OK;

@@ -272,9 +272,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) batch_kernel(const BatchA
     }
     __syncthreads();
     if (!s_ok) break;
-    const uint32_t first = (uint32_t)(t - L.tile0) * (uint32_t)a.tile_slots;
+    const uint32_t per = (uint32_t)a.tile_slots[L.D() == 3 ? 1 : 0];
+    const uint32_t first = (uint32_t)(t - L.tile0) * per;
     const uint32_t slots = pair_slots(L);
-    const uint32_t end = first + (uint32_t)a.tile_slots < slots ? first + (uint32_t)a.tile_slots : slots;
+    const uint32_t end = first + per < slots ? first + per : slots;
     const unsigned long long step = (unsigned long long)(step0 + s);
     const uint32_t lo = (uint32_t)step, hi = (uint32_t)(step >> 32);
     if (step & 1)
@@ -312,9 +313,10 @@ __global__ void __launch_bounds__(MINB >= 5 ? 128 : kBatchMaxThreads, MINB)
   const int t = tile_base + (int)blockIdx.x;
   const int lat = lattice_of(a, t, lat_lo, lat_hi);
   const BatchLattice &L = a.lats[lat];
-  const uint32_t first = (uint32_t)(t - L.tile0) * (uint32_t)a.tile_slots;
+  const uint32_t per = (uint32_t)a.tile_slots[D == 3 ? 1 : 0];
+  const uint32_t first = (uint32_t)(t - L.tile0) * per;
   const uint32_t slots = pair_slots(L);
-  const uint32_t end = first + (uint32_t)a.tile_slots < slots ? first + (uint32_t)a.tile_slots : slots;
+  const uint32_t end = first + per < slots ? first + per : slots;
   const uint32_t slot = first + threadIdx.x;
   if (slot >= end) return;
   const unsigned long long step = (unsigned long long)(*a.step_counter + k);
@@ -363,12 +365,13 @@ cudaError_t launch_group_any(int form, bool shear, int parity, const BatchArgs &
                 : launch_group<D, false, 0>(form, a, k, g, threads, s);
 }
 
-cudaError_t launch_batch_steps(int form, bool shear, int parity0, const BatchArgs &a, const BatchGroup &g3,
-                               const BatchGroup &g2, int n, int threads, cudaStream_t s) {
+cudaError_t launch_batch_steps(int form3, int threads3, int form2, int threads2, bool shear, int parity0,
+                               const BatchArgs &a, const BatchGroup &g3, const BatchGroup &g2, int n,
+                               cudaStream_t s) {
   for (int k = 0; k < n; ++k) {
     const int parity = (parity0 + k) & 1;
-    cudaError_t e = launch_group_any<3>(form, shear, parity, a, k, g3, threads, s);
-    if (e == cudaSuccess) e = launch_group_any<2>(form, shear, parity, a, k, g2, threads, s);
+    cudaError_t e = launch_group_any<3>(form3, shear, parity, a, k, g3, threads3, s);
+    if (e == cudaSuccess) e = launch_group_any<2>(form2, shear, parity, a, k, g2, threads2, s);
     if (e != cudaSuccess) return e;
   }
   batch_advance_kernel<<<1, 1, 0, s>>>(a.step_counter, n);

@@ -67,7 +67,8 @@ struct BatchArgs {
   const float *rates;        // general rates: om[27] then phc[27] per lattice (device)
   char *pool;                // the allocation holding every lattice's populations
   int nlat, ntiles, nsteps;  // lattices, tiles (all lattices), steps of this launch
-  int tile_slots;            // pair slots (two x-adjacent sites) per tile = threads per block
+  int tile_slots[2];         // pair slots (two x-adjacent sites) per tile = threads per block:
+                             // [0] the D2Q9 lattices, [1] the D3Q27 lattices
   long long *step_counter;   // device: completed steps of every lattice
   int *done;                 // device, one per lattice, zero at launch: tiles finished
   unsigned int *exits;       // device, zero at launch: blocks that have left
@@ -92,10 +93,11 @@ enum BatchForm {
   kBatchStepRolled = 3,  // per-step launches, 128-register cap, rolled D3Q27 noise
   kBatchFormMax = 3
 };
-// n steps as plain launches (per step one launch per lattice type, block = tile), then
-// the step-counter update.
-cudaError_t launch_batch_steps(int form, bool shear, int parity0, const BatchArgs &a, const BatchGroup &g3,
-                               const BatchGroup &g2, int n, int threads, cudaStream_t s);
+// n steps as plain launches (per step one launch per lattice type, block = tile, each
+// type in its own per-step form and block size), then the step-counter update.
+cudaError_t launch_batch_steps(int form3, int threads3, int form2, int threads2, bool shear, int parity0,
+                               const BatchArgs &a, const BatchGroup &g3, const BatchGroup &g2, int n,
+                               cudaStream_t s);
 
 // Statistics accumulators, in doubles: see stats.cu for the layout.
 int stats_nacc(int Q);

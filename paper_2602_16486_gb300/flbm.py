@@ -122,6 +122,9 @@ def _load():
         "flbm_batch_get_step": (ctypes.c_int64, [vp]),
         "flbm_batch_set_shape": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
         "flbm_batch_get_shape": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "flbm_batch_set_type_shape": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "flbm_batch_get_type_shape": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                     ctypes.POINTER(ctypes.c_int)]),
         "flbm_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int)]),
         "flbm_batch_uses_graph": (ctypes.c_int, [vp]),
@@ -418,6 +421,17 @@ def flbm_batch_get_shape(b):
     return t.value, f.value
 
 
+def flbm_batch_set_type_shape(b, lattice, threads, form):
+    _check(_lib.flbm_batch_set_type_shape(b, int(lattice), int(threads), int(form)))
+
+
+def flbm_batch_get_type_shape(b, lattice):
+    t = ctypes.c_int(-1)
+    f = ctypes.c_int(-1)
+    _check(_lib.flbm_batch_get_type_shape(b, int(lattice), ctypes.byref(t), ctypes.byref(f)))
+    return t.value, f.value
+
+
 def flbm_batch_autotune(b, trial_steps=10):
     """Returns (threads, form) of the fastest launch shape."""
     t = ctypes.c_int(-1)
@@ -666,6 +680,13 @@ class Batch:
     @shape.setter
     def shape(self, tf):
         flbm_batch_set_shape(self.handle, tf[0], tf[1])
+
+    def type_shape(self, lattice):
+        """(threads per block, launch form) of one lattice type as launched."""
+        return flbm_batch_get_type_shape(self.handle, lattice)
+
+    def set_type_shape(self, lattice, threads, form):
+        flbm_batch_set_type_shape(self.handle, lattice, threads, form)
 
     def autotune(self, trial_steps=10):
         return flbm_batch_autotune(self.handle, trial_steps)

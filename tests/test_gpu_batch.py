@@ -161,6 +161,34 @@ def test_batch_shapes_same_result(fl, threads, form):
         assert np.array_equal(g, r)
 
 
+@pytest.mark.parametrize("shape3,shape2", [((128, 0), (64, 2)), ((64, 3), (256, 0)), ((128, 2), (128, 3))])
+def test_batch_type_shapes_same_result(fl, shape3, shape2):
+    # Each lattice type in its own per-step shape computes the same update, bit for bit;
+    # the persistent form refuses per-type shapes and launches every type alike.
+    specs = _specs(False)
+    with fl.Batch(specs) as b:
+        _init(b)
+        b.set_type_shape(fl.FLBM_D3Q27, *shape3)
+        b.set_type_shape(fl.FLBM_D2Q9, *shape2)
+        assert b.type_shape(fl.FLBM_D3Q27) == shape3 and b.type_shape(fl.FLBM_D2Q9) == shape2
+        assert b.shape == shape3
+        b.step(3)
+        b.step(4)
+        b.sync()
+        got = [b.lattice(i).populations() for i in range(len(specs))]
+        b.shape = (128, 1)
+        assert b.type_shape(fl.FLBM_D2Q9) == (128, 1)
+        with pytest.raises(fl.FlbmError) as e:
+            b.set_type_shape(fl.FLBM_D2Q9, 64, 0)
+        assert e.value.status == fl.FLBM_ESTATE
+    with fl.Batch(specs) as b:
+        _init(b)
+        b.step(7)
+        ref = [b.lattice(i).populations() for i in range(len(specs))]
+    for g, r in zip(got, ref):
+        assert np.array_equal(g, r)
+
+
 def test_batch_autotune_leaves_state(fl):
     specs = _specs(False)
     with fl.Batch(specs) as b:
